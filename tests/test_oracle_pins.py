@@ -1,0 +1,489 @@
+"""Pins for the FP64 oracle: checks against things other than the oracle itself.
+
+Each test ties an oracle function to a closed form, an invariant, a library routine, brute
+force on a tiny input or a value the paper prints, so that a plausible slip (a dropped term,
+a wrong sign or index, a transposed operand, a wrong weight) fails at least one of them.
+
+  function              pinned by
+  --------------------  ------------------------------------------------------------------
+  philox4x64_10         numpy.random.Philox (independent implementation), exact words
+  u01 / probes          range, exact +-1 values, moments within 4 SE, E[r r^T] = I
+  cov_matrix            closed forms (n=1, coincident points, distance l), scipy cdist,
+                        symmetry, positive definiteness (eigvalsh >= lambda)
+  cov_matrix(which)     central finite differences of K in psi; dK/dlog lambda = lambda I;
+                        dK/dlog sigma^2 = K - lambda I
+  kmv / dkmv_all        dense matrix product with numpy on tiny and ragged sizes
+  exact_gradient        central finite differences of the log marginal likelihood
+  log_marginal_lik.     scipy.stats.multivariate_normal.logpdf
+  cg_record             Cholesky solution (Sec. 3 error definition), conjugacy and residual
+                        orthogonality, n=1 in one step, K ~ c I in one step
+  draw_J                P(J >= j) = exp(-beta j (j+1)/2) within 4 SE; expected tail length
+                        vs the paper's printed 1.4 at beta = 1 (tests/golden)
+  ulisse_solve          reconstruction from the recorded CG trajectory; exact expectation by
+                        enumerating J equals the converged CG solution; mean of 10^4 seeded
+                        estimates within 4 SE (exact covariance) of the Cholesky solution
+  grad_estimate         mean of 10^4 seeded estimates within 4 SE of the exact gradient;
+                        Hutchinson identity by enumerating all sign vectors
+  chol / sgld_update    numpy.linalg.cholesky; closed-form update with the drawn noise;
+                        stationary moments of a Gaussian target
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_X(n, d, seed, scale=1.0):
+    return np.random.default_rng(seed).uniform(0.0, scale, (n, d))
+
+
+# ----------------------------------------------------------------------------------------
+# Random numbers
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ctr,key", [
+    ((1, 0, 0, 0), (0, 0)),
+    ((6, 7, 9, 11), (123, 456)),
+    ((2**64 - 1, 2**63, 12345, 2**40 + 3), (2**64 - 1, 20150122)),
+    ((977, 3, 20150123, 2 | (1 << 8)), (20150123, 0)),
+])
+def test_philox_matches_numpy(orc, ctr, key):
+    # numpy's Philox pre-increments its counter: its first block is philox(counter + 1).
+    c = list(ctr)
+    c[0] = (c[0] - 1) % 2**64
+    if ctr[0] == 0:
+        pytest.skip("borrow case not needed")
+    ref = np.random.Philox(counter=np.array(c, dtype=np.uint64),
+                          key=np.array(key, dtype=np.uint64)).random_raw(4)
+    got = orc.philox4x64_10(ctr, key)
+    assert [int(x) for x in got] == [int(x) for x in ref]
+
+
+def test_u01_range_and_moments(orc):
+    words = np.random.Philox(key=[7, 9]).random_raw(200_000)
+    u = np.array([orc.u01(int(w)) for w in words[:20000]])
+    assert u.min() >= 0.0 and u.max() < 1.0
+    n = len(u)
+    assert abs(u.mean() - 0.5) < 4 * math.sqrt(1 / 12 / n)
+    assert abs(u.var() - 1 / 12) < 4 * math.sqrt(1 / 180 / n)
+    # exact dyadic values: top 53 bits scaled by 2^-53
+    assert orc.u01(0) == 0.0
+    assert orc.u01(2**64 - 1) == (2**53 - 1) / 2**53
+
+
+def test_probes_rademacher(orc):
+    n, nr = 257, 3
+    r = orc.probes(n, nr, 0, seed=11, epoch=5)
+    assert r.shape == (n, nr)
+    assert set(np.unique(r)) == {-1.0, 1.0}
+    # E[r r^T] = I (Sec. 2.1): average outer products over many epochs of a short probe.
+    m, reps = 6, 4000
+    acc = np.zeros((m, m))
+    for e in range(reps):
+        v = orc.probes(m, 1, 0, seed=3, epoch=e)[:, 0]
+        acc += np.outer(v, v)
+    acc /= reps
+    assert np.allclose(np.diag(acc), 1.0)
+    off = acc[~np.eye(m, dtype=bool)]
+    assert np.max(np.abs(off)) < 4.5 / math.sqrt(reps)
+    # different epochs / columns / seeds give different probes
+    assert not np.array_equal(orc.probes(n, 1, 0, 11, 5), orc.probes(n, 1, 0, 11, 6))
+    assert not np.array_equal(r[:, 0], r[:, 1])
+
+
+def test_probes_gaussian_moments(orc):
+    z = orc.probes(50_000, 2, 1, seed=5, epoch=0).ravel()
+    n = z.size
+    assert abs(z.mean()) < 4 / math.sqrt(n)
+    assert abs(z.var() - 1) < 4 * math.sqrt(2 / n)
+    kurt = np.mean(z**4)
+    assert abs(kurt - 3) < 4 * math.sqrt(96 / n)
+
+
+# ----------------------------------------------------------------------------------------
+# Covariance (Eq. covariance:rbf, ARD reading)
+# ----------------------------------------------------------------------------------------
+def test_cov_closed_forms(orc):
+    psi = np.log([0.7, 1.3, 2.0, 0.25])   # l1, l2, sigma^2, lambda
+    K = orc.cov_matrix(np.array([[0.3, -0.2]]), psi)
+    assert K.shape == (1, 1) and abs(K[0, 0] - (2.0 + 0.25)) < 1e-15
+    # coincident points: off-diagonal = sigma^2
+    K = orc.cov_matrix(np.array([[0.1, 0.2], [0.1, 0.2]]), psi)
+    assert abs(K[0, 1] - 2.0) < 1e-15 and abs(K[0, 0] - 2.25) < 1e-15
+    # points one lengthscale apart along dim 0: sigma^2 e^{-1/2}
+    K = orc.cov_matrix(np.array([[0.0, 0.0], [0.7, 0.0]]), psi)
+    assert abs(K[0, 1] - 2.0 * math.exp(-0.5)) < 1e-14
+    # along dim 1 by 2 l2: sigma^2 e^{-2}
+    K = orc.cov_matrix(np.array([[0.0, 0.0], [0.0, 2.6]]), psi)
+    assert abs(K[1, 0] - 2.0 * math.exp(-2.0)) < 1e-14
+
+
+def test_cov_vs_scipy_cdist(orc):
+    from scipy.spatial.distance import cdist
+    X = _rand_X(37, 3, 1)
+    psi = np.log([0.3, 0.5, 0.9, 1.7, 0.05])
+    ls = np.exp(psi[:3])
+    ref = 1.7 * np.exp(-0.5 * cdist(X / ls, X / ls, "sqeuclidean")) + 0.05 * np.eye(37)
+    K = orc.cov_matrix(X, psi)
+    assert np.max(np.abs(K - ref)) < 1e-14
+    assert np.array_equal(K, K.T)
+    assert np.linalg.eigvalsh(K).min() >= 0.05 * (1 - 1e-9)
+
+
+@pytest.mark.parametrize("which", [0, 1, 2, 3, 4])
+def test_dK_vs_finite_differences(orc, which):
+    X = _rand_X(9, 3, 2)
+    psi = np.log([0.4, 0.8, 0.6, 1.3, 0.2])
+    h = 1e-5
+    pp, pm = psi.copy(), psi.copy()
+    pp[which] += h
+    pm[which] -= h
+    fd = (orc.cov_matrix(X, pp) - orc.cov_matrix(X, pm)) / (2 * h)
+    dK = orc.cov_matrix(X, psi, which=which)
+    assert np.max(np.abs(fd - dK)) < 1e-8
+
+
+def test_dK_closed_forms(orc):
+    X = _rand_X(11, 2, 3)
+    psi = np.log([0.4, 0.8, 1.6, 0.3])
+    K = orc.cov_matrix(X, psi)
+    assert np.allclose(orc.cov_matrix(X, psi, which=3), 0.3 * np.eye(11), rtol=0, atol=1e-15)
+    assert np.allclose(orc.cov_matrix(X, psi, which=2), K - 0.3 * np.eye(11), rtol=0, atol=1e-15)
+    for q in range(2):
+        assert np.all(np.diag(orc.cov_matrix(X, psi, which=q)) == 0.0)
+
+
+@pytest.mark.parametrize("n,d,R", [(1, 1, 1), (5, 2, 3), (67, 3, 4), (130, 8, 2)])
+def test_kmv_vs_dense(orc, n, d, R):
+    X = _rand_X(n, d, 4 + n)
+    psi = np.concatenate([np.log(np.full(d, 0.5)), [np.log(1.2), np.log(0.1)]])
+    V = np.random.default_rng(n).standard_normal((n, R))
+    for which in [-1] + list(range(d + 2)):
+        dense = orc.cov_matrix(X, psi, which) @ V
+        got = orc.kmv(X, psi, V, which)
+        assert np.max(np.abs(got - dense)) <= 1e-12 * max(1.0, np.max(np.abs(dense)))
+    allp = orc.dkmv_all(X, psi, V)
+    for q in range(d + 2):
+        dense = orc.cov_matrix(X, psi, q) @ V
+        assert np.max(np.abs(allp[q] - dense)) <= 1e-12 * max(1.0, np.max(np.abs(dense)))
+
+
+# ----------------------------------------------------------------------------------------
+# Exact path (Sec. 2)
+# ----------------------------------------------------------------------------------------
+def test_log_marginal_likelihood_vs_scipy(orc):
+    from scipy.stats import multivariate_normal
+    X = _rand_X(40, 2, 5)
+    psi = np.log([0.3, 0.6, 1.1, 0.2])
+    y = np.random.default_rng(5).standard_normal(40)
+    K = orc.cov_matrix(X, psi)
+    ref = multivariate_normal(mean=np.zeros(40), cov=K).logpdf(y)
+    assert abs(orc.log_marginal_likelihood(X, y, psi) - ref) < 1e-9 * abs(ref)
+
+
+def test_exact_gradient_vs_fd_of_log_marginal_likelihood(orc):
+    X = _rand_X(60, 3, 6)
+    psi = np.log([0.35, 0.5, 0.8, 1.4, 0.15])
+    y = np.random.default_rng(6).standard_normal(60)
+    g = orc.exact_gradient(X, y, psi)
+    h = 1e-5
+    fd = np.zeros_like(psi)
+    for i in range(len(psi)):
+        pp, pm = psi.copy(), psi.copy()
+        pp[i] += h
+        pm[i] -= h
+        fd[i] = (orc.log_marginal_likelihood(X, y, pp) - orc.log_marginal_likelihood(X, y, pm)) / (2 * h)
+    assert np.max(np.abs(g - fd)) < 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+# ----------------------------------------------------------------------------------------
+# CG (Algorithm 1)
+# ----------------------------------------------------------------------------------------
+def test_cg_converges_to_cholesky(orc):
+    X = _rand_X(80, 2, 7)
+    psi = np.log([0.3, 0.3, 1.0, 0.1])
+    b = np.random.default_rng(7).standard_normal(80)
+    tr = orc.cg_record(X, psi, b, eps=1e-10)
+    exact = orc.exact_solve(X, psi, b)
+    assert np.linalg.norm(tr["S"][-1] - exact) < 1e-7 * np.linalg.norm(exact)
+    assert np.linalg.norm(tr["E"][-1]) < 1e-10
+
+
+def test_cg_invariants(orc):
+    X = _rand_X(50, 2, 8)
+    psi = np.log([0.5, 0.5, 1.0, 0.5])     # well conditioned: orthogonality holds to rounding
+    b = np.random.default_rng(8).standard_normal(50)
+    tr = orc.cg_record(X, psi, b, eps=1e-12)
+    K = orc.cov_matrix(X, psi)
+    k = min(6, tr["T"])
+    Dm, Em = tr["D"][:k], tr["E"][:k]
+    G = Dm @ K @ Dm.T
+    off = G - np.diag(np.diag(G))
+    assert np.max(np.abs(off)) < 1e-9 * np.max(np.diag(G))
+    H = Em @ Em.T
+    offe = H - np.diag(np.diag(H))
+    assert np.max(np.abs(offe)) < 1e-9 * np.max(np.diag(H))
+    # residual recurrence equals the true residual b - K s
+    for i in range(k):
+        assert np.linalg.norm(tr["E"][i] - (b - K @ tr["S"][i])) < 1e-10 * np.linalg.norm(b)
+
+
+def test_cg_single_step_cases(orc):
+    # n = 1: one step gives b / K
+    X = np.array([[0.2, 0.4]])
+    psi = np.log([0.5, 0.5, 2.0, 0.5])
+    tr = orc.cg_record(X, psi, np.array([3.0]))
+    assert tr["T"] == 1 and abs(tr["S"][-1][0] - 3.0 / 2.5) < 1e-15
+    # far-apart points: K = (sigma^2 + lambda) I up to e^{-huge}; one step
+    X = np.arange(10, dtype=float)[:, None] * 100.0
+    psi = np.log([0.1, 1.5, 0.5])
+    b = np.random.default_rng(9).standard_normal(10)
+    tr = orc.cg_record(X, psi, b)
+    assert tr["T"] == 1 and np.allclose(tr["S"][-1], b / 2.0, rtol=1e-15, atol=0)
+
+
+# ----------------------------------------------------------------------------------------
+# ULISSE (Sec. 4)
+# ----------------------------------------------------------------------------------------
+def _read_golden(name):
+    vals = {}
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            k, v = line.split("=", 1)
+            vals[k.strip()] = float(v)
+    return vals
+
+
+def test_expected_tail_length_matches_paper(orc):
+    g = _read_golden("ulisse_tail_length.txt")
+    # the paper's rounded value for beta = 1
+    assert abs(orc.expected_tail_steps(1.0) - g["expected_tail_steps_beta1"]) < g["tolerance"]
+    # and the closed form of the same sum: sum_j exp(-beta j (j+1) / 2)
+    cf = sum(math.exp(-j * (j + 1) / 2) for j in range(60))
+    assert abs(orc.expected_tail_steps(1.0) - cf) < 1e-12
+
+
+@pytest.mark.parametrize("beta", [1.0, 0.3])
+def test_J_distribution(orc, beta):
+    N = 20000
+    Js = np.array([orc.draw_J(99, step, colid=5, est=0, beta=beta) for step in range(N)])
+    for j in range(1, 5):
+        p = math.exp(-beta * j * (j + 1) / 2)
+        emp = np.mean(Js >= j)
+        assert abs(emp - p) < 4 * math.sqrt(p * (1 - p) / N) + 1e-12
+    # estimators 0 and 1 of the same column draw independently
+    J0 = [orc.draw_J(1, s, 0, 0, beta) for s in range(3000)]
+    J1 = [orc.draw_J(1, s, 0, 1, beta) for s in range(3000)]
+    assert abs(np.corrcoef(J0, J1)[0, 1]) < 4 / math.sqrt(3000)
+
+
+def _trajectory(orc, X, psi, b, eps):
+    tr = orc.cg_record(X, psi, b, eps=eps)
+    S = tr["S"]
+    delta = np.diff(S, axis=0)           # delta_i = s_i - s_{i-1}, i = 1..T
+    norms = np.linalg.norm(tr["E"], axis=1)
+    return tr, S, delta, norms
+
+
+def test_ulisse_reconstruction_from_trajectory(orc):
+    n = 60
+    X = _rand_X(n, 2, 10)
+    psi = np.log([0.25, 0.25, 1.0, 0.05])
+    b = np.random.default_rng(10).choice([-1.0, 1.0], n)
+    q, beta, eps = 0.3, 1.0, 1e-10
+    tr, S, delta, norms = _trajectory(orc, X, psi, b, eps)
+    alpha = q * math.sqrt(n)
+    l = next(i for i in range(1, tr["T"] + 1) if norms[i] < alpha)
+    R = 200
+    B = np.repeat(b[:, None], R, axis=1)
+    S_est, st = orc.ulisse_solve(X, psi, B, colid=np.arange(R), q=q, beta=beta, eps=eps,
+                                 seed=4, step=17)
+    for c in range(R):
+        J = int(st[c, 3])
+        assert st[c, 0] == l
+        ref = S[l].copy()
+        for j in range(1, J + 1):
+            if l + j > tr["T"]:
+                break
+            ref += orc.weight_product(j, beta) * delta[l + j - 1]
+        assert np.linalg.norm(S_est[:, c] - ref) < 1e-9 * np.linalg.norm(ref)
+        assert st[c, 1] == min(l + J, tr["T"])
+
+
+def test_ulisse_expectation_by_enumeration(orc):
+    """E[s~] over the exact law of J equals the converged CG solution s_T."""
+    n = 40
+    X = _rand_X(n, 2, 11)
+    psi = np.log([0.3, 0.3, 1.0, 0.3])
+    b = np.random.default_rng(11).standard_normal(n)
+    q, beta = 0.5, 1.0
+    tr, S, delta, norms = _trajectory(orc, X, psi, b, 1e-11)
+    T = tr["T"]
+    l = next(i for i in range(1, T + 1) if norms[i] < q * math.sqrt(n))
+    # every J in 0..T-l has a representable probability, so the enumeration is complete
+    assert T - l <= 30, (T, l)
+    mean = np.zeros(n)
+    for J in range(0, T - l + 1):
+        pJ = math.exp(-beta * J * (J + 1) / 2) - (math.exp(-beta * (J + 1) * (J + 2) / 2)
+                                                  if J < T - l else 0.0)
+        est = S[l].copy()
+        for j in range(1, J + 1):
+            est += orc.weight_product(j, beta) * delta[l + j - 1]
+        mean += pJ * est
+    assert np.linalg.norm(mean - S[T]) < 1e-9 * np.linalg.norm(S[T])
+    exact = orc.exact_solve(X, psi, b)
+    assert np.linalg.norm(mean - exact) < 1e-7 * np.linalg.norm(exact)
+
+
+def test_ulisse_unbiased_statistical(orc):
+    """Mean of 10^4 seeded ULISSE estimates within 4 SE of the Cholesky solution, with the
+    SE from the exact covariance Cov(s~) = sum_{j,k} (W_min(j,k) - 1) delta_j delta_k^T."""
+    n = 48
+    X = _rand_X(n, 2, 12)
+    psi = np.log([0.3, 0.3, 1.0, 0.05])
+    b = np.random.default_rng(12).choice([-1.0, 1.0], n)
+    q, beta, eps = 0.5, 1.0, 1e-11
+    tr, S, delta, norms = _trajectory(orc, X, psi, b, eps)
+    T = tr["T"]
+    l = next(i for i in range(1, T + 1) if norms[i] < q * math.sqrt(n))
+    N = 10000
+    B = np.repeat(b[:, None], N, axis=1)
+    S_est, st = orc.ulisse_solve(X, psi, B, colid=np.arange(N), q=q, beta=beta, eps=eps,
+                                 seed=2024, step=3)
+    var = np.zeros(n)
+    for j in range(1, T - l + 1):
+        for k in range(1, T - l + 1):
+            W = orc.weight_product(min(j, k), beta)
+            var += (W - 1.0) * delta[l + j - 1] * delta[l + k - 1]
+    se = np.sqrt(var / N)
+    exact = orc.exact_solve(X, psi, b)
+    z = (S_est.mean(axis=1) - exact) / np.maximum(se, 1e-300)
+    assert np.max(np.abs(z)) < 4.0
+    # the estimator is not degenerate: it really varies
+    assert np.max(np.std(S_est, axis=1)) > 0
+    # plain CG would need T iterations; ULISSE's mean cost is l + E[J]
+    assert st[:, 1].mean() < T
+
+
+def test_hutchinson_identity_exhaustive(orc):
+    """Sec. 2.1: E[r^T A r] = Tr(A) for +-1 probes, checked by enumerating all 2^n vectors."""
+    n = 10
+    X = _rand_X(n, 2, 13)
+    psi = np.log([0.4, 0.4, 1.0, 0.1])
+    K = orc.cov_matrix(X, psi)
+    A = np.linalg.solve(K, orc.cov_matrix(X, psi, which=0))
+    tot = 0.0
+    for m in range(2**n):
+        r = np.array([1.0 if (m >> i) & 1 else -1.0 for i in range(n)])
+        tot += r @ A @ r
+    assert abs(tot / 2**n - np.trace(A)) < 1e-10 * max(1.0, abs(np.trace(A)))
+    assert abs(np.trace(A) - orc.exact_trace_term(X, psi, 0)) < 1e-10 * max(1.0, abs(np.trace(A)))
+
+
+@pytest.mark.slow
+def test_grad_estimate_unbiased(orc):
+    """E[g~] = g (Eq. gradient:unbiased vs Eq. gradient:exact): mean of 10^4 seeded
+    estimates within 4 standard errors of the Cholesky gradient."""
+    n = 64
+    rng = np.random.default_rng(14)
+    X = rng.uniform(0, 1, (n, 2))
+    psi = np.log([0.3, 0.4, 1.0, 0.1])
+    y = np.linalg.cholesky(orc.cov_matrix(X, psi)) @ rng.standard_normal(n)
+    g = orc.exact_gradient(X, y, psi)
+    N = 10000
+    G = np.array([orc.grad_estimate(X, y, psi, nr=2, q=0.5, beta=1.0, eps=1e-11, seed=77,
+                                    step=s)[0] for s in range(N)])
+    se = G.std(axis=0, ddof=1) / math.sqrt(N)
+    z = (G.mean(axis=0) - g) / se
+    assert np.max(np.abs(z)) < 4.0, (G.mean(axis=0), g, se)
+
+
+def test_grad_estimate_without_truncation_is_hutchinson(orc):
+    """With q -> 0 (no early stop) every solve is the converged CG solution, so g~ is the
+    plain Hutchinson estimate; with the probes fixed it is a closed form in K."""
+    n = 30
+    rng = np.random.default_rng(15)
+    X = rng.uniform(0, 1, (n, 2))
+    psi = np.log([0.5, 0.5, 1.0, 0.2])
+    y = rng.standard_normal(n)
+    nr = 3
+    g, st = orc.grad_estimate(X, y, psi, nr=nr, q=0.0, eps=1e-12, seed=5, step=9)
+    r = orc.probes(n, nr, 0, 5, 9)
+    K = orc.cov_matrix(X, psi)
+    a = np.linalg.solve(K, y)
+    for i in range(4):
+        dK = orc.cov_matrix(X, psi, which=i)
+        tr = sum(np.linalg.solve(K, r[:, j]) @ dK @ r[:, j] for j in range(nr)) / nr
+        ref = -0.5 * tr + 0.5 * a @ dK @ a
+        assert abs(g[i] - ref) < 1e-8 * max(1.0, abs(ref))
+    assert np.all(st[:, 0] == 0)        # early stop never reached
+
+
+# ----------------------------------------------------------------------------------------
+# SGLD (Sec. 2.1)
+# ----------------------------------------------------------------------------------------
+def test_chol_vs_numpy(orc):
+    A = np.random.default_rng(16).standard_normal((7, 7))
+    M = A @ A.T + 7 * np.eye(7)
+    assert np.allclose(orc.chol(M), np.linalg.cholesky(M), rtol=0, atol=1e-13)
+    with pytest.raises(np.linalg.LinAlgError):
+        orc.chol(-np.eye(3))
+
+
+def test_sgld_update_closed_form(orc):
+    p = 5
+    rng = np.random.default_rng(17)
+    psi = rng.standard_normal(p)
+    g = rng.standard_normal(p)
+    A = rng.standard_normal((p, p))
+    M = A @ A.T + np.eye(p)
+    pg = rng.standard_normal(p)
+    eps_t = 3e-3
+    xi = orc.sgld_noise(8, 21, p)
+    out = orc.sgld_update(psi, g, eps_t, M=M, prior_grad=pg, seed=8, step=21)
+    ref = psi + 0.5 * eps_t * M @ (g + pg) + math.sqrt(eps_t) * np.linalg.cholesky(M) @ xi
+    assert np.allclose(out, ref, rtol=0, atol=1e-14)
+    out = orc.sgld_update(psi, g, eps_t, seed=8, step=21)
+    assert np.allclose(out, psi + 0.5 * eps_t * g + math.sqrt(eps_t) * xi, rtol=0, atol=1e-14)
+
+
+def test_sgld_noise_moments(orc):
+    Z = np.array([orc.sgld_noise(3, s, 4) for s in range(20000)])
+    N = Z.shape[0]
+    assert np.max(np.abs(Z.mean(axis=0))) < 4 / math.sqrt(N)
+    C = np.cov(Z.T)
+    assert np.max(np.abs(np.diag(C) - 1)) < 4 * math.sqrt(2 / N)
+    assert np.max(np.abs(C - np.diag(np.diag(C)))) < 4 / math.sqrt(N)
+
+
+def test_sgld_stationary_gaussian(orc):
+    """With the exact gradient of a Gaussian log density, small-step SGLD leaves
+    N(mu, Sigma) (approximately) invariant: the chain's mean and covariance match."""
+    mu = np.array([0.5, -1.0])
+    Sigma = np.array([[1.0, 0.6], [0.6, 2.0]])
+    P = np.linalg.inv(Sigma)
+    M = Sigma.copy()                      # preconditioner = posterior covariance
+    eps_t = 0.02
+    psi = mu.copy()
+    N = 60000
+    out = np.empty((N, 2))
+    for t in range(N):
+        g = -P @ (psi - mu)
+        psi = orc.sgld_update(psi, g, eps_t, M=M, seed=12, step=t)
+        out[t] = psi
+    burn = out[1000:]
+    # effective sample size: with M = Sigma the chain is an AR(1) with rho = 1 - eps/2
+    rho = 1 - eps_t / 2
+    ess = len(burn) * (1 - rho) / (1 + rho)
+    se_mean = np.sqrt(np.diag(Sigma) / ess)
+    assert np.all(np.abs(burn.mean(axis=0) - mu) < 4 * se_mean)
+    C = np.cov(burn.T)
+    # discretisation bias of the Euler step is O(eps); allow 4 SE + 2 eps relative
+    for i in range(2):
+        se_var = Sigma[i, i] * math.sqrt(2 / ess)
+        assert abs(C[i, i] - Sigma[i, i]) < 4 * se_var + 2 * eps_t * Sigma[i, i]
