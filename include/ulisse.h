@@ -1,0 +1,204 @@
+/*
+ * ulisse.h -- C ABI of libulisse, a GB300 (sm_103a) implementation of the hot path of
+ * "Enabling scalable stochastic gradient-based inference for Gaussian processes by
+ * employing the Unbiased LInear System SolvEr (ULISSE)" (Filippone & Engler, ICML 2015).
+ *
+ * The library samples GP covariance parameters with stochastic gradient Langevin dynamics
+ * (SGLD, Sec. 2.1).  Each gradient is the unbiased estimate of Eq. gradient:unbiased, built
+ * from ULISSE solves (Sec. 4) of K s = y and K s = r_j for Hutchinson probes r_j; every
+ * solve iterates matrix-free covariance products K V (Sec. 3), generated tile by tile on the
+ * GPU and never stored.
+ *
+ * Model (Eq. covariance:rbf, read as the decaying ARD squared exponential; Sec. 6 names the
+ * ARD extension):
+ *     k(x_i, x_j) = sigma^2 exp(-1/2 sum_d (x_id - x_jd)^2 / l_d^2) + lambda delta_ij
+ * Parameters are psi = log theta = (log l_1 .. log l_d, log sigma^2, log lambda), p = d + 2;
+ * derivatives are taken with respect to psi (dK/dpsi_i = theta_i dK/dtheta_i).
+ *
+ * Conventions for every call:
+ *   - Pointers marked "device" are CUDA device pointers on the context's device; "host"
+ *     pointers are ordinary host memory (pinned or pageable).  The caller owns every buffer
+ *     it passes; the context owns its own scratch.
+ *   - Blocks of vectors are column-major: column c of an n x R block starts at c * n
+ *     (leading dimension n).  float unless stated otherwise.
+ *   - All GPU work is ordered on the stream given to ulisse_create (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  Calls that return host results
+ *     synchronise that stream before returning.
+ *   - Every call returns a ulisse_status and never aborts.  ulisse_last_error gives a
+ *     message for the last failing call.  Kernels report breakdowns through a device status
+ *     word that the next synchronising call reads; no kernel traps.
+ *   - Results are deterministic for a given (seed, step): random draws come from a
+ *     counter-based generator (Philox4x64-10) and reductions use a fixed order.
+ *   - Not thread-safe per context: calls on one context must not overlap.
+ */
+#ifndef ULISSE_H
+#define ULISSE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ulisse_ctx ulisse_ctx;
+
+typedef enum {
+    ULISSE_OK = 0,
+    ULISSE_ERR_ARG = 1,       /* invalid argument (null pointer, size out of range, ...) */
+    ULISSE_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    ULISSE_ERR_BREAKDOWN = 3, /* CG breakdown: d^T K d <= 0 or a non-finite value (K not
+                                 positive definite along d, or NaN in the inputs) */
+    ULISSE_ERR_MAXITER = 4,   /* a solve hit max_iter before its stopping rule: the
+                                 estimate is returned but is not unbiased */
+    ULISSE_ERR_NOMEM = 5,     /* device allocation failed */
+    ULISSE_ERR_TIMEOUT = 6    /* a bounded device wait ran out (the kernel returned early) */
+} ulisse_status;
+
+typedef enum {
+    ULISSE_PREC_FP32 = 0,     /* FP32 vectors and SIMT products, FP64 scalar recurrences */
+    ULISSE_PREC_MIXED = 1,    /* tensor-core (tcgen05) products, FP32 vectors */
+    ULISSE_PREC_FP64 = 2      /* FP64 everywhere (the paper's double-precision CMVPs) */
+} ulisse_precision;
+
+typedef enum {
+    ULISSE_PROBE_RADEMACHER = 0, /* entries +-1 with probability 1/2 (Sec. 2.1) */
+    ULISSE_PROBE_GAUSSIAN = 1    /* entries N(0,1); also E[r r^T] = I */
+} ulisse_probe_kind;
+
+typedef struct {
+    int precision;           /* ulisse_precision */
+    int n_probes;            /* N_r >= 1, Hutchinson probes per gradient (Eq. gradient:unbiased) */
+    int probe_kind;          /* ulisse_probe_kind */
+    int probe_refresh;       /* redraw the probes every probe_refresh steps (>= 1; the paper's
+                                Concrete run used 20, Sec. 5.1); epoch = step / probe_refresh */
+    int warm_start_probes;   /* nonzero: while the probes are unchanged, start each probe
+                                solve from the previous step's final CG iterate (Sec. 5.1) */
+    double q;                /* early-stop threshold alpha = q sqrt(n) (Sec. 4; the paper uses q=1) */
+    double beta;             /* ULISSE weights w_r = exp(beta r) (Sec. 4; the paper uses beta=1) */
+    double eps;              /* CG convergence threshold on ||e|| (Algorithm 1; paper: 1e-8) */
+    int max_iter;            /* cap on CG iterations per solve (>= 1) */
+    unsigned long long seed; /* key of the counter-based generator */
+} ulisse_config;
+
+/* Fill *cfg with the paper's settings: FP32, 4 Rademacher probes redrawn every step,
+ * q = 1, beta = 1, eps = 1e-8, max_iter = 1000, seed 0. */
+void ulisse_config_default(ulisse_config *cfg);
+
+/*
+ * Create a context for one GP regression problem (Sec. 2: labels y for inputs X).
+ *   X      device, n x d float, ROW-major (point i at X + i*d); copied into the context.
+ *   y      device, n floats; copied into the context.
+ *   n      number of inputs, 1 <= n <= 2^31 - 1.
+ *   d      input dimension, 1 <= d <= 16.
+ *   cfg    host; copied.  stream: cudaStream_t (as void*) for all later work.
+ * The context selects the current CUDA device at creation and uses it for its lifetime.
+ * Errors: ULISSE_ERR_ARG (null pointers, n or d out of range, bad cfg), ULISSE_ERR_NOMEM.
+ */
+ulisse_status ulisse_create(ulisse_ctx **out, const float *X, const float *y, long long n,
+                            int d, const ulisse_config *cfg, void *stream);
+
+/* As ulisse_create, but X and y are HOST arrays (row-major n x d, and n). */
+ulisse_status ulisse_create_host(ulisse_ctx **out, const float *X, const float *y,
+                                 long long n, int d, const ulisse_config *cfg, void *stream);
+
+/*
+ * Covariance matrix-vector products without storing K (Sec. 3; Algorithm 1's CMVP):
+ *     U = A V,  A = K(psi) if which == -1, else A = dK/dpsi_which (0 <= which < d+2).
+ *   psi  host, p = d+2 doubles.
+ *   V    device, n x R column-major (leading dimension n), R >= 1.
+ *   U    device, n x R column-major; must not overlap V.
+ * In FP64 precision V and U are read and written as float and converted; use
+ * ulisse_kmv_f64 for double data.  Asynchronous on the context's stream.
+ * Errors: ULISSE_ERR_ARG (which out of range, R < 1, null, non-finite psi).
+ */
+ulisse_status ulisse_kmv(ulisse_ctx *ctx, const double *psi, int which, const float *V, int R,
+                         float *U);
+
+/* As ulisse_kmv with double V and U (computed in FP64 on the GPU). */
+ulisse_status ulisse_kmv_f64(ulisse_ctx *ctx, const double *psi, int which, const double *V,
+                             int R, double *U);
+
+/* Per-column outcome of a solve, written to host memory when requested. */
+typedef struct {
+    int l;          /* early-stop iteration (first i >= 1 with ||e_i|| < q sqrt(n)); 0 = never */
+    int iterations; /* CG iterations run for the column */
+    int outcome;    /* ULISSE_OK, ULISSE_ERR_BREAKDOWN or ULISSE_ERR_MAXITER */
+    int J0, J1;     /* accepted steps after the early stop, estimator 0 and 1 (-1 if absent) */
+} ulisse_col_stats;
+
+/*
+ * ULISSE solve (Sec. 4): unbiased estimates of K(psi)^{-1} B[:, c] for every column c.
+ * Each column runs Algorithm 1; after the early-stop threshold is reached at iteration l,
+ * step j is kept with probability 1/w_j and reweighted by prod_{r<=j} w_r.
+ *   psi       host, p doubles.
+ *   B         device, n x R column-major right-hand sides, 1 <= R <= 1024.
+ *   n_est     host, R ints in {1, 2}: independent estimators per column (NULL = all 1).  Two
+ *             estimators share one CG run and differ only in their uniforms (Sec. 4.1).
+ *   S0        device, n x R initial iterates, or NULL for zero.
+ *   S_est     device, n x sum(n_est) column-major: the estimators of column 0, then of
+ *             column 1, ...
+ *   step      counter for the random draws (uniforms for column c, estimator t, step j come
+ *             from Philox counter (j, c, step, 2 | t << 8)).
+ *   stats     host, R entries, or NULL.
+ * Synchronises the stream.  Returns ULISSE_ERR_BREAKDOWN / ULISSE_ERR_MAXITER if any column
+ * ended that way (all outputs are still written).
+ */
+ulisse_status ulisse_solve(ulisse_ctx *ctx, const double *psi, const float *B, int R,
+                           const int *n_est, const float *S0, float *S_est,
+                           unsigned long long step, ulisse_col_stats *stats);
+
+/*
+ * Unbiased gradient estimate g~ of log p(y | theta) with respect to psi
+ * (Eq. gradient:unbiased):
+ *     g~_i = 1/2 a1^T dK_i a2 - 1/(2 N_r) sum_j z_j^T dK_i r_j
+ * with a1, a2 two independent ULISSE estimates of K^{-1} y from one CG run (Sec. 4.1), z_j
+ * the ULISSE estimate of K^{-1} r_j, and probes r_j drawn for epoch step / probe_refresh
+ * (probe column j >= 1, element i from Philox counter (i, j, epoch, 1)).
+ *   psi   host, p doubles.   g  host, p doubles (output).   stats: host, 1 + N_r, or NULL.
+ * Synchronises the stream.
+ */
+ulisse_status ulisse_grad(ulisse_ctx *ctx, const double *psi, unsigned long long step,
+                          double *g, ulisse_col_stats *stats);
+
+/*
+ * One SGLD step (Sec. 2.1) on psi:
+ *     psi <- psi + eps_t/2 M (g~ + grad log p(psi)) + sqrt(eps_t) L xi,   L L^T = M,
+ * xi ~ N(0, I_p) from Philox counter (k, 0, step, 3) by the Box-Muller transform; all
+ * proposals are accepted (Sec. 2.1).
+ *   psi_inout   host, p doubles, updated in place.
+ *   M           host, p x p row-major symmetric positive definite, or NULL for I.
+ *   prior_grad  host, p doubles of grad_psi log p(psi), or NULL for a flat prior in psi.
+ *   g_out       host, p doubles (the g~ used), or NULL.
+ * Synchronises the stream.  ULISSE_ERR_ARG if M is not positive definite.
+ */
+ulisse_status ulisse_sgld_step(ulisse_ctx *ctx, double *psi_inout, double eps_t,
+                               const double *M, const double *prior_grad,
+                               unsigned long long step, double *g_out);
+
+/*
+ * n_steps SGLD steps with psi resident on the device (no host round trip per step):
+ *   psi_dev     device, p doubles, updated in place.
+ *   eps_dev     device, n_steps doubles: step size of each step.
+ *   M           host, p x p or NULL (fixed for the run).  prior_grad: host p or NULL (fixed).
+ *   trace_dev   device, n_steps x p doubles (psi after each step), or NULL.
+ *   step0       step counter of the first step.
+ * Asynchronous with respect to the host except for one status read at the end.
+ */
+ulisse_status ulisse_sgld_chain(ulisse_ctx *ctx, double *psi_dev, const double *eps_dev,
+                                int n_steps, const double *M, const double *prior_grad,
+                                unsigned long long step0, double *trace_dev);
+
+/* Number of K V products (one per CG iteration of the batched solve, all live columns at
+ * once) and of generated kernel entries times right-hand sides since creation. */
+ulisse_status ulisse_counters(const ulisse_ctx *ctx, long long *mvp_rounds,
+                              double *entry_rhs);
+
+/* Message for the last failing call on ctx (or on creation if ctx is NULL). */
+const char *ulisse_last_error(const ulisse_ctx *ctx);
+
+/* Free the context and all of its device memory.  NULL is allowed. */
+void ulisse_destroy(ulisse_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ULISSE_H */

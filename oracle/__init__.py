@@ -62,6 +62,8 @@ def _load():
             lib.orc_cov_matrix.argtypes = [P, L, I, P, I, P]
             lib.orc_kmv.argtypes = [P, L, I, P, I, P, I, P]
             lib.orc_dkmv_all.argtypes = [P, L, I, P, P, I, P]
+            lib.orc_kmv_rows.argtypes = [P, L, I, P, I, P, I, P, L, P]
+            lib.orc_kmv_rows_abs.argtypes = [P, L, I, P, I, P, I, P, L, P]
             lib.orc_probes.argtypes = [L, I, I, U64, U64, P]
             lib.orc_draw_J.argtypes = [U64, U64, U64, I, D, I]
             lib.orc_draw_J.restype = I
@@ -155,6 +157,19 @@ def kmv(X, psi, V, which=-1):
     _load().orc_kmv(_ptr(X), n, d, _ptr(psi), which, _ptr(Vc), R, _ptr(U))
     out = U.T.copy()
     return out[:, 0] if np.asarray(V).ndim == 1 else out
+
+
+def kmv_rows(X, psi, V, rows, which=-1, absolute=False):
+    """Rows `rows` of K V (or dK/dpsi_which V); absolute=True gives sum_j |A_ij| |V_jr|."""
+    X = _f64(X)
+    n, d = X.shape
+    psi = _f64(psi)
+    Vc, R = _colmajor(V, n)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    U = np.zeros((R, len(rows)))
+    fn = _load().orc_kmv_rows_abs if absolute else _load().orc_kmv_rows
+    fn(_ptr(X), n, d, _ptr(psi), which, _ptr(Vc), R, _ptr(rows), len(rows), _ptr(U))
+    return U.T.copy()
 
 
 def dkmv_all(X, psi, V):

@@ -161,6 +161,41 @@ void orc_kmv(const double *X, long n, int d, const double *psi, int which,
     }
 }
 
+/* The same product restricted to the output rows listed in rows[0..nrows-1]:
+ * U[k + r*nrows] = sum_j A[rows[k], j] V[j, r]  (for checks of large problems). */
+void orc_kmv_rows(const double *X, long n, int d, const double *psi, int which,
+                  const double *V, int R, const long *rows, long nrows, double *U)
+{
+    orc_theta t = unpack(psi, d);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long k = 0; k < nrows; ++k) {
+        const long i = rows[k];
+        for (int r = 0; r < R; ++r) {
+            double acc = 0.0;
+            for (long j = 0; j < n; ++j) acc += entry(X, i, j, &t, which) * V[(long)r * n + j];
+            U[(long)r * nrows + k] = acc;
+        }
+    }
+}
+
+/* Sum over j of |A[i,j]| |V[j,r]| for the listed rows: the scale of each output entry's
+ * rounding error (a dot product's condition). */
+void orc_kmv_rows_abs(const double *X, long n, int d, const double *psi, int which,
+                      const double *V, int R, const long *rows, long nrows, double *U)
+{
+    orc_theta t = unpack(psi, d);
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long k = 0; k < nrows; ++k) {
+        const long i = rows[k];
+        for (int r = 0; r < R; ++r) {
+            double acc = 0.0;
+            for (long j = 0; j < n; ++j)
+                acc += fabs(entry(X, i, j, &t, which)) * fabs(V[(long)r * n + j]);
+            U[(long)r * nrows + k] = acc;
+        }
+    }
+}
+
 /* All p derivative products in one sweep over the entries:
  * U_all[q] (n x R, col-major, q = 0..p-1) = dK/dpsi_q V. */
 void orc_dkmv_all(const double *X, long n, int d, const double *psi,

@@ -1,0 +1,755 @@
+// C ABI of libulisse (include/ulisse.h): context management and the host-side ordering of
+// the kernels for one K V product, one ULISSE solve, one gradient and one SGLD step.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ulisse.h"
+#include "solver_kernels.cuh"
+
+using namespace ulisse;
+
+struct ulisse_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  long long n = 0, ldn = 0;
+  int d = 0, DP = 0;
+  ulisse_config cfg{};
+  bool f64 = false;
+  size_t esz = 4;
+
+  float* X = nullptr;         // raw inputs, n x d row-major
+  void* y = nullptr;          // labels, ldn (element type T)
+  void* xhat = nullptr;       // prescaled inputs, ldn x DP
+  DevParams* params = nullptr;
+  double* psi_dev = nullptr;  // kMaxP
+
+  int cap = 0;                // column capacity of B, S, E, D, KD
+  int cap_est = 0;            // column capacity of SE
+  void *B = nullptr, *S = nullptr, *E = nullptr, *D = nullptr, *KD = nullptr, *SE = nullptr;
+  ColState* st = nullptr;
+  int* live = nullptr;
+  int* n_live_dev = nullptr;
+  int* iota = nullptr;        // 0, 1, 2, ... (cap entries)
+  int* h_n_live = nullptr;    // pinned
+
+  void* partials = nullptr;
+  size_t partials_bytes = 0;
+  int* counters = nullptr;
+  int counters_len = 0;
+
+  double* gpart = nullptr;
+  size_t gpart_len = 0;
+  int* gcounter = nullptr;
+  double* g_dev = nullptr;
+  void* sa_dev = nullptr;     // gradient scales (T), kMaxM
+  int* amap = nullptr;        // gradient left-factor columns
+  int* bmap = nullptr;        // gradient right-factor columns
+  int grad_nr = -1;           // probe count the maps were built for
+
+  double* M_dev = nullptr;
+  double* prior_dev = nullptr;
+  int* status_dev = nullptr;
+  int* h_status = nullptr;    // pinned
+
+  long long mvp_rounds = 0;
+  double entry_rhs = 0.0;
+  std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+#define CK(call)                                                                     \
+  do {                                                                               \
+    cudaError_t e_ = (call);                                                         \
+    if (e_ != cudaSuccess) {                                                         \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return e_ == cudaErrorMemoryAllocation ? ULISSE_ERR_NOMEM : ULISSE_ERR_CUDA;   \
+    }                                                                                \
+  } while (0)
+
+#define CKS(expr)                          \
+  do {                                     \
+    ulisse_status s_ = (expr);             \
+    if (s_ != ULISSE_OK) return s_;        \
+  } while (0)
+
+static ulisse_status fail(ulisse_ctx* ctx, ulisse_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+static int dp_for(int d) { return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : 16; }
+
+static ulisse_status dev_alloc(ulisse_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return ULISSE_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(ctx, ULISSE_ERR_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemsetAsync(*p, 0, bytes, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, ULISSE_ERR_CUDA, cudaGetErrorString(e));
+  return ULISSE_OK;
+}
+
+static void dev_free(void*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Column buffers for at least R solver columns and R_est estimate columns.
+static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
+  if (R <= ctx->cap && R_est <= ctx->cap_est) return ULISSE_OK;
+  const int cap = std::max(R, ctx->cap), cap_est = std::max(R_est, ctx->cap_est);
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (void** p : {&ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD, &ctx->SE}) dev_free(*p);
+  dev_free(reinterpret_cast<void*&>(ctx->st));
+  dev_free(reinterpret_cast<void*&>(ctx->live));
+  dev_free(reinterpret_cast<void*&>(ctx->iota));
+  const size_t col = (size_t)ctx->ldn * ctx->esz;
+  for (void** p : {&ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD})
+    CKS(dev_alloc(ctx, p, col * cap));
+  CKS(dev_alloc(ctx, &ctx->SE, col * cap_est));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->st), sizeof(ColState) * cap));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->live), sizeof(int) * cap));
+  const int ni = std::max(cap, cap_est);
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->iota), sizeof(int) * ni));
+  std::vector<int> io(ni);
+  for (int i = 0; i < ni; ++i) io[i] = i;
+  CK(cudaMemcpyAsync(ctx->iota, io.data(), sizeof(int) * ni, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->cap = cap;
+  ctx->cap_est = cap_est;
+  return ULISSE_OK;
+}
+
+static bool finite_psi(const double* psi, int p) {
+  for (int i = 0; i < p; ++i)
+    if (!std::isfinite(psi[i])) return false;
+  return true;
+}
+
+// psi (host) -> device, then the prescale kernel (a1).
+static ulisse_status set_psi_host(ulisse_ctx* ctx, const double* psi) {
+  const int p = ctx->d + 2;
+  if (!psi || !finite_psi(psi, p)) return fail(ctx, ULISSE_ERR_ARG, "psi is null or not finite");
+  CK(cudaMemcpyAsync(ctx->psi_dev, psi, sizeof(double) * p, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  return ULISSE_OK;
+}
+
+static ulisse_status prescale(ulisse_ctx* ctx) {
+  const int blocks = (int)std::min<long long>((ctx->n + 255) / 256, 4LL * ctx->num_sms);
+  if (ctx->f64)
+    prescale_kernel<double><<<blocks, 256, 0, ctx->stream>>>(
+        ctx->psi_dev, ctx->X, (double*)ctx->xhat, ctx->n, ctx->d, ctx->DP, ctx->params);
+  else
+    prescale_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
+        ctx->psi_dev, ctx->X, (float*)ctx->xhat, ctx->n, ctx->d, ctx->DP, ctx->params);
+  CK(cudaGetLastError());
+  return ULISSE_OK;
+}
+
+// U[:, umap[r]] = A V[:, vmap[r]] for r < R (chunks of kMaxRChunk columns per launch).
+static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, int R, void* U,
+                             const int* umap, int mode, int which) {
+  for (int c0 = 0; c0 < R; c0 += kMaxRChunk) {
+    KmvLaunch L{};
+    L.xhat = ctx->xhat;
+    L.n = ctx->n;
+    L.ldn = ctx->ldn;
+    L.d = ctx->d;
+    L.DP = ctx->DP;
+    L.V = V;
+    L.ldv = ctx->ldn;
+    L.vmap = vmap + c0;
+    L.R = std::min(kMaxRChunk, R - c0);
+    L.U = U;
+    L.ldu = ctx->ldn;
+    L.umap = umap + c0;
+    L.params = ctx->params;
+    L.mode = mode;
+    L.which = which;
+    L.status = ctx->status_dev;
+    L.num_sms = ctx->num_sms;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      L.partials = ctx->partials;
+      L.partials_bytes = ctx->partials_bytes;
+      L.counters = ctx->counters;
+      L.counters_len = ctx->counters_len;
+      cudaError_t e = ctx->f64 ? launch_kmv_f64(L, ctx->stream) : launch_kmv_f32(L, ctx->stream);
+      if (e == cudaSuccess) break;
+      if (e != cudaErrorMemoryAllocation || attempt == 1)
+        return fail(ctx, ULISSE_ERR_CUDA, std::string("K V launch: ") + cudaGetErrorString(e));
+      cudaGetLastError();
+      // Grow the split-j scratch to what this launch needs, then retry.
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (L.need_partials_bytes > ctx->partials_bytes) {
+        dev_free(ctx->partials);
+        ctx->partials_bytes = 0;
+        CKS(dev_alloc(ctx, &ctx->partials, L.need_partials_bytes));
+        ctx->partials_bytes = L.need_partials_bytes;
+      }
+      if (L.need_counters > ctx->counters_len) {
+        dev_free(reinterpret_cast<void*&>(ctx->counters));
+        ctx->counters_len = 0;
+        CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->counters),
+                      sizeof(int) * L.need_counters));
+        ctx->counters_len = L.need_counters;
+      }
+    }
+    ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
+  }
+  return ULISSE_OK;
+}
+
+static ulisse_status read_status(ulisse_ctx* ctx, int* status) {
+  CK(cudaMemcpyAsync(ctx->h_status, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *status = *ctx->h_status;
+  return ULISSE_OK;
+}
+
+static ulisse_status status_to_result(ulisse_ctx* ctx, int s) {
+  if (s & kStatusTimeout) return fail(ctx, ULISSE_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (s & kStatusBadM) return fail(ctx, ULISSE_ERR_ARG, "M is not positive definite");
+  if (s & kStatusBreakdown)
+    return fail(ctx, ULISSE_ERR_BREAKDOWN, "CG breakdown (d^T K d <= 0 or non-finite)");
+  if (s & kStatusMaxIter) return fail(ctx, ULISSE_ERR_MAXITER, "a solve reached max_iter");
+  return ULISSE_OK;
+}
+
+template <typename T>
+static CgArgs<T> cg_args(ulisse_ctx* ctx, int has_s0, unsigned long long step) {
+  CgArgs<T> a;
+  a.S = (T*)ctx->S;
+  a.E = (T*)ctx->E;
+  a.D = (T*)ctx->D;
+  a.KD = (const T*)ctx->KD;
+  a.B = (const T*)ctx->B;
+  a.SE = (T*)ctx->SE;
+  a.n = ctx->n;
+  a.ld = ctx->ldn;
+  a.st = ctx->st;
+  a.live = ctx->live;
+  a.alpha_thr = ctx->cfg.q * std::sqrt((double)ctx->n);
+  a.eps = ctx->cfg.eps;
+  a.beta = ctx->cfg.beta;
+  a.max_iter = ctx->cfg.max_iter;
+  a.has_s0 = has_s0;
+  a.seed = ctx->cfg.seed;
+  a.step = step;
+  a.status = ctx->status_dev;
+  return a;
+}
+
+// Column metadata (estimator count, estimator offset, random-stream column) for R columns.
+static ulisse_status upload_meta(ulisse_ctx* ctx, int R, const int* n_est, int* total_est) {
+  std::vector<ColState> h(R);
+  int off = 0;
+  for (int c = 0; c < R; ++c) {
+    std::memset(&h[c], 0, sizeof(ColState));
+    h[c].n_est = n_est ? n_est[c] : 1;
+    h[c].est_off = off;
+    h[c].colid = c;
+    off += h[c].n_est;
+  }
+  CK(cudaMemcpyAsync(ctx->st, h.data(), sizeof(ColState) * R, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *total_est = off;
+  return ULISSE_OK;
+}
+
+// Batched CG + ULISSE on columns 0..R-1 of B (S holds s_0 when has_s0).  The host learns
+// the live count after every iteration and launches K V on the live columns only.
+template <typename T>
+static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned long long step) {
+  CgArgs<T> a = cg_args<T>(ctx, has_s0, step);
+  if (has_s0) {
+    CKS(run_kmv(ctx, ctx->S, ctx->iota, R, ctx->KD, ctx->iota, kModeK, -1));
+    ctx->mvp_rounds += 1;
+  }
+  cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
+  CK(cudaGetLastError());
+  for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
+    compact_kernel<<<1, 32, 0, ctx->stream>>>(ctx->st, R, ctx->live, ctx->n_live_dev);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->h_n_live, ctx->n_live_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int nl = *ctx->h_n_live;
+    if (nl == 0) break;
+    CKS(run_kmv(ctx, ctx->D, ctx->live, nl, ctx->KD, ctx->live, kModeK, -1));
+    ctx->mvp_rounds += 1;
+    cg_iter_kernel<T><<<nl, kCgNT, 0, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+  }
+  return ULISSE_OK;
+}
+
+static ulisse_status solve_dispatch(ulisse_ctx* ctx, int R, int has_s0,
+                                    unsigned long long step) {
+  return ctx->f64 ? solve_core<double>(ctx, R, has_s0, step)
+                  : solve_core<float>(ctx, R, has_s0, step);
+}
+
+// Gradient column maps: left factors SE[0] (a1) and SE[2..1+nr] (z_j) with scales 1/2 and
+// -1/(2 nr); right factors B[0] (a2, copied there after the solve) and B[1..nr] (r_j).
+static ulisse_status ensure_grad_maps(ulisse_ctx* ctx, int nr) {
+  if (ctx->grad_nr == nr) return ULISSE_OK;
+  const int M = 1 + nr;
+  std::vector<int> am(M), bm(M);
+  std::vector<float> sf(M);
+  std::vector<double> sd(M);
+  for (int m = 0; m < M; ++m) {
+    am[m] = (m == 0) ? 0 : m + 1;
+    bm[m] = m;
+    const double s = (m == 0) ? 0.5 : -1.0 / (2.0 * nr);
+    sf[m] = (float)s;
+    sd[m] = s;
+  }
+  CK(cudaMemcpyAsync(ctx->amap, am.data(), sizeof(int) * M, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->bmap, bm.data(), sizeof(int) * M, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  if (ctx->f64)
+    CK(cudaMemcpyAsync(ctx->sa_dev, sd.data(), sizeof(double) * M, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  else
+    CK(cudaMemcpyAsync(ctx->sa_dev, sf.data(), sizeof(float) * M, cudaMemcpyHostToDevice,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->grad_nr = nr;
+  return ULISSE_OK;
+}
+
+static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
+  GradLaunch L{};
+  L.xhat = ctx->xhat;
+  L.n = ctx->n;
+  L.ldn = ctx->ldn;
+  L.d = ctx->d;
+  L.DP = ctx->DP;
+  L.A = ctx->SE;
+  L.amap = ctx->amap;
+  L.sa = ctx->sa_dev;
+  L.B = ctx->B;
+  L.bmap = ctx->bmap;
+  L.ld = ctx->ldn;
+  L.M = M;
+  L.params = ctx->params;
+  L.counter = ctx->gcounter;
+  L.g_out = ctx->g_dev;
+  L.status = ctx->status_dev;
+  L.num_sms = ctx->num_sms;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    L.partials = ctx->gpart;
+    L.partials_len = ctx->gpart_len;
+    cudaError_t e = ctx->f64 ? launch_grad_f64(L, ctx->stream) : launch_grad_f32(L, ctx->stream);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorMemoryAllocation || attempt == 1)
+      return fail(ctx, ULISSE_ERR_CUDA, std::string("gradient launch: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    CK(cudaStreamSynchronize(ctx->stream));
+    dev_free(reinterpret_cast<void*&>(ctx->gpart));
+    ctx->gpart_len = 0;
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gpart), sizeof(double) * L.need_partials_len));
+    ctx->gpart_len = L.need_partials_len;
+  }
+  ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)M;
+  return ULISSE_OK;
+}
+
+// Whole gradient path for one step (a1..a6): psi must already be in psi_dev.
+static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step) {
+  const int nr = ctx->cfg.n_probes, R = 1 + nr;
+  CKS(ensure_columns(ctx, R, R + 1));
+  CKS(ensure_grad_maps(ctx, nr));
+  CKS(prescale(ctx));
+  // B[0] = y, B[1..nr] = probes for this epoch
+  CK(cudaMemcpyAsync(ctx->B, ctx->y, ctx->ldn * ctx->esz, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  const unsigned long long epoch = step / (unsigned long long)ctx->cfg.probe_refresh;
+  dim3 pg((unsigned)std::min<long long>((ctx->n + 255) / 256, 2LL * ctx->num_sms), nr);
+  if (ctx->f64)
+    probes_kernel<double><<<pg, 256, 0, ctx->stream>>>((double*)ctx->B, ctx->ldn, ctx->n, nr,
+                                                        ctx->cfg.probe_kind, ctx->cfg.seed, epoch);
+  else
+    probes_kernel<float><<<pg, 256, 0, ctx->stream>>>((float*)ctx->B, ctx->ldn, ctx->n, nr,
+                                                       ctx->cfg.probe_kind, ctx->cfg.seed, epoch);
+  CK(cudaGetLastError());
+  std::vector<int> n_est(R, 1);
+  n_est[0] = 2;
+  int tot = 0;
+  CKS(upload_meta(ctx, R, n_est.data(), &tot));
+  CKS(solve_dispatch(ctx, R, 0, step));
+  // a2 (second estimate of K^{-1} y) becomes the right factor of the quadratic term.
+  CK(cudaMemcpyAsync(ctx->B, (char*)ctx->SE + ctx->ldn * ctx->esz, ctx->ldn * ctx->esz,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CKS(run_grad(ctx, R));
+  return ULISSE_OK;
+}
+
+static ulisse_status check_cfg(const ulisse_config* c) {
+  if (!c) return ULISSE_ERR_ARG;
+  if (c->precision < 0 || c->precision > 2) return ULISSE_ERR_ARG;
+  if (c->n_probes < 1 || c->n_probes > kMaxM - 1) return ULISSE_ERR_ARG;
+  if (c->probe_kind < 0 || c->probe_kind > 1) return ULISSE_ERR_ARG;
+  if (c->probe_refresh < 1 || c->max_iter < 1) return ULISSE_ERR_ARG;
+  if (!(c->q >= 0.0) || !(c->beta > 0.0) || !(c->eps >= 0.0)) return ULISSE_ERR_ARG;
+  if (!std::isfinite(c->q) || !std::isfinite(c->beta) || !std::isfinite(c->eps))
+    return ULISSE_ERR_ARG;
+  return ULISSE_OK;
+}
+
+static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* y, long long n,
+                                 int d, const ulisse_config* cfg, void* stream,
+                                 cudaMemcpyKind kind) {
+  if (!out) return fail(nullptr, ULISSE_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (!X || !y) return fail(nullptr, ULISSE_ERR_ARG, "X or y is null");
+  if (n < 1 || n > 2147483647LL) return fail(nullptr, ULISSE_ERR_ARG, "n out of range");
+  if (d < 1 || d > kMaxD) return fail(nullptr, ULISSE_ERR_ARG, "d must be in 1..16");
+  if (check_cfg(cfg) != ULISSE_OK) return fail(nullptr, ULISSE_ERR_ARG, "invalid config");
+  if (cfg->precision == ULISSE_PREC_MIXED)
+    return fail(nullptr, ULISSE_ERR_ARG, "mixed precision is not available in this build");
+  if (cfg->warm_start_probes)
+    return fail(nullptr, ULISSE_ERR_ARG, "warm_start_probes is not available in this build");
+  ulisse_ctx* ctx = new ulisse_ctx();
+  ctx->stream = (cudaStream_t)stream;
+  ctx->cfg = *cfg;
+  ctx->n = n;
+  ctx->d = d;
+  ctx->DP = dp_for(d);
+  ctx->ldn = (n + kBN - 1) / kBN * kBN;
+  ctx->f64 = cfg->precision == ULISSE_PREC_FP64;
+  ctx->esz = ctx->f64 ? 8 : 4;
+  auto bail = [&](ulisse_status s) {
+    g_create_error = ctx->err;
+    ulisse_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+          cudaSuccess) {
+    ctx->err = "no CUDA device";
+    return bail(ULISSE_ERR_CUDA);
+  }
+  ulisse_status s;
+  if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->X), sizeof(float) * n * d)) ||
+      (s = dev_alloc(ctx, &ctx->y, ctx->ldn * ctx->esz)) ||
+      (s = dev_alloc(ctx, &ctx->xhat, ctx->ldn * ctx->DP * ctx->esz)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->params), sizeof(DevParams))) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->psi_dev), sizeof(double) * kMaxP)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->n_live_dev), sizeof(int))) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gcounter), sizeof(int))) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->g_dev), sizeof(double) * kMaxP)) ||
+      (s = dev_alloc(ctx, &ctx->sa_dev, sizeof(double) * kMaxM)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->amap), sizeof(int) * kMaxM)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bmap), sizeof(int) * kMaxM)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->M_dev), sizeof(double) * kMaxP * kMaxP)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->prior_dev), sizeof(double) * kMaxP)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))))
+    return bail(s);
+  if (cudaMallocHost(&ctx->h_n_live, sizeof(int)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) {
+    ctx->err = "cudaMallocHost failed";
+    return bail(ULISSE_ERR_NOMEM);
+  }
+  // Inputs: X as given (row-major float); y into the context's element type.
+  if (cudaMemcpyAsync(ctx->X, X, sizeof(float) * n * d, kind, ctx->stream) != cudaSuccess) {
+    ctx->err = "copy of X failed";
+    return bail(ULISSE_ERR_CUDA);
+  }
+  if (!ctx->f64) {
+    if (cudaMemcpyAsync(ctx->y, y, sizeof(float) * n, kind, ctx->stream) != cudaSuccess) {
+      ctx->err = "copy of y failed";
+      return bail(ULISSE_ERR_CUDA);
+    }
+  } else {
+    float* tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(float) * n) != cudaSuccess) {
+      ctx->err = "cudaMalloc failed";
+      return bail(ULISSE_ERR_NOMEM);
+    }
+    cudaMemcpyAsync(tmp, y, sizeof(float) * n, kind, ctx->stream);
+    convert_cols_kernel<float, double><<<dim3(64, 1), 256, 0, ctx->stream>>>(
+        tmp, n, (double*)ctx->y, ctx->ldn, n);
+    cudaStreamSynchronize(ctx->stream);
+    cudaFree(tmp);
+  }
+  if ((s = ensure_columns(ctx, 1 + cfg->n_probes, 2 + cfg->n_probes))) return bail(s);
+  if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    ctx->err = "stream synchronisation failed";
+    return bail(ULISSE_ERR_CUDA);
+  }
+  *out = ctx;
+  return ULISSE_OK;
+}
+
+extern "C" {
+
+void ulisse_config_default(ulisse_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = ULISSE_PREC_FP32;
+  cfg->n_probes = 4;
+  cfg->probe_kind = ULISSE_PROBE_RADEMACHER;
+  cfg->probe_refresh = 1;
+  cfg->warm_start_probes = 0;
+  cfg->q = 1.0;
+  cfg->beta = 1.0;
+  cfg->eps = 1e-8;
+  cfg->max_iter = 1000;
+  cfg->seed = 0;
+}
+
+ulisse_status ulisse_create(ulisse_ctx** out, const float* X, const float* y, long long n, int d,
+                            const ulisse_config* cfg, void* stream) {
+  return create_impl(out, X, y, n, d, cfg, stream, cudaMemcpyDeviceToDevice);
+}
+
+ulisse_status ulisse_create_host(ulisse_ctx** out, const float* X, const float* y, long long n,
+                                 int d, const ulisse_config* cfg, void* stream) {
+  return create_impl(out, X, y, n, d, cfg, stream, cudaMemcpyHostToDevice);
+}
+
+static ulisse_status copy_stats(ulisse_ctx* ctx, ulisse_col_stats* stats, int R) {
+  if (!stats) return ULISSE_OK;
+  std::vector<ColState> h(R);
+  CK(cudaMemcpyAsync(h.data(), ctx->st, sizeof(ColState) * R, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int c = 0; c < R; ++c) {
+    stats[c].l = h[c].l;
+    stats[c].iterations = h[c].m;
+    stats[c].outcome = h[c].outcome;
+    stats[c].J0 = h[c].J[0];
+    stats[c].J1 = h[c].n_est > 1 ? h[c].J[1] : -1;
+  }
+  return ULISSE_OK;
+}
+
+static ulisse_status kmv_common(ulisse_ctx* ctx, const double* psi, int which, const void* V,
+                                int R, void* U, bool f64_data) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!V || !U || R < 1 || R > 4096) return fail(ctx, ULISSE_ERR_ARG, "V/U null or R out of range");
+  if (which < -1 || which > ctx->d + 1) return fail(ctx, ULISSE_ERR_ARG, "which out of range");
+  if (f64_data && !ctx->f64)
+    return fail(ctx, ULISSE_ERR_ARG, "double data needs a context created with FP64 precision");
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  CKS(ensure_columns(ctx, R, R));
+  const long long n = ctx->n;
+  const size_t ue = f64_data ? 8 : 4;
+  // caller's V (leading dimension n) -> context buffer D (leading dimension ldn)
+  if (ctx->esz == ue) {
+    CK(cudaMemcpy2DAsync(ctx->D, ctx->ldn * ctx->esz, V, n * ue, n * ue, R,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    convert_cols_kernel<float, double><<<dim3(64, R), 256, 0, ctx->stream>>>(
+        (const float*)V, n, (double*)ctx->D, ctx->ldn, n);
+    CK(cudaGetLastError());
+  }
+  int mode = kModeK, w = -1;
+  if (which >= 0 && which < ctx->d) { mode = kModeDLen; w = which; }
+  else if (which == ctx->d) mode = kModeDSig;
+  else if (which == ctx->d + 1) mode = 3;
+  CKS(run_kmv(ctx, ctx->D, ctx->iota, R, ctx->KD, ctx->iota, mode, w));
+  if (ctx->esz == ue) {
+    CK(cudaMemcpy2DAsync(U, n * ue, ctx->KD, ctx->ldn * ctx->esz, n * ue, R,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    convert_cols_kernel<double, float><<<dim3(64, R), 256, 0, ctx->stream>>>(
+        (const double*)ctx->KD, ctx->ldn, (float*)U, n, n);
+    CK(cudaGetLastError());
+  }
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_kmv(ulisse_ctx* ctx, const double* psi, int which, const float* V, int R,
+                         float* U) {
+  return kmv_common(ctx, psi, which, V, R, U, false);
+}
+
+ulisse_status ulisse_kmv_f64(ulisse_ctx* ctx, const double* psi, int which, const double* V,
+                             int R, double* U) {
+  return kmv_common(ctx, psi, which, V, R, U, true);
+}
+
+ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, int R,
+                           const int* n_est, const float* S0, float* S_est,
+                           unsigned long long step, ulisse_col_stats* stats) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!B || !S_est || R < 1 || R > 1024) return fail(ctx, ULISSE_ERR_ARG, "B/S_est null or R out of range");
+  int tot = 0;
+  if (n_est)
+    for (int c = 0; c < R; ++c) {
+      if (n_est[c] < 1 || n_est[c] > 2) return fail(ctx, ULISSE_ERR_ARG, "n_est must be 1 or 2");
+      tot += n_est[c];
+    }
+  else tot = R;
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  CKS(ensure_columns(ctx, R, tot));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  const long long n = ctx->n;
+  auto in_cols = [&](const float* src, void* dst) -> ulisse_status {
+    if (!ctx->f64) {
+      CK(cudaMemcpy2DAsync(dst, ctx->ldn * 4, src, n * 4, n * 4, R, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    } else {
+      convert_cols_kernel<float, double><<<dim3(64, R), 256, 0, ctx->stream>>>(
+          src, n, (double*)dst, ctx->ldn, n);
+      CK(cudaGetLastError());
+    }
+    return ULISSE_OK;
+  };
+  CKS(in_cols(B, ctx->B));
+  if (S0) CKS(in_cols(S0, ctx->S));
+  CKS(upload_meta(ctx, R, n_est, &tot));
+  CKS(solve_dispatch(ctx, R, S0 ? 1 : 0, step));
+  if (!ctx->f64) {
+    CK(cudaMemcpy2DAsync(S_est, n * 4, ctx->SE, ctx->ldn * 4, n * 4, tot,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  } else {
+    convert_cols_kernel<double, float><<<dim3(64, tot), 256, 0, ctx->stream>>>(
+        (const double*)ctx->SE, ctx->ldn, S_est, n, n);
+    CK(cudaGetLastError());
+  }
+  CKS(copy_stats(ctx, stats, R));
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+ulisse_status ulisse_grad(ulisse_ctx* ctx, const double* psi, unsigned long long step, double* g,
+                          ulisse_col_stats* stats) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!g) return fail(ctx, ULISSE_ERR_ARG, "g is null");
+  CKS(set_psi_host(ctx, psi));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  CKS(grad_core(ctx, step));
+  CK(cudaMemcpyAsync(g, ctx->g_dev, sizeof(double) * (ctx->d + 2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CKS(copy_stats(ctx, stats, 1 + ctx->cfg.n_probes));
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+static ulisse_status upload_M_prior(ulisse_ctx* ctx, const double* M, const double* prior,
+                                    const double** Md, const double** pd) {
+  const int p = ctx->d + 2;
+  *Md = nullptr;
+  *pd = nullptr;
+  if (M) {
+    for (int i = 0; i < p * p; ++i)
+      if (!std::isfinite(M[i])) return fail(ctx, ULISSE_ERR_ARG, "M not finite");
+    CK(cudaMemcpyAsync(ctx->M_dev, M, sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    *Md = ctx->M_dev;
+  }
+  if (prior) {
+    if (!finite_psi(prior, p)) return fail(ctx, ULISSE_ERR_ARG, "prior_grad not finite");
+    CK(cudaMemcpyAsync(ctx->prior_dev, prior, sizeof(double) * p, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    *pd = ctx->prior_dev;
+  }
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t, const double* M,
+                               const double* prior_grad, unsigned long long step, double* g_out) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!(eps_t >= 0.0) || !std::isfinite(eps_t)) return fail(ctx, ULISSE_ERR_ARG, "eps_t invalid");
+  CKS(set_psi_host(ctx, psi_inout));
+  const double *Md, *pd;
+  CKS(upload_M_prior(ctx, M, prior_grad, &Md, &pd));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  CKS(grad_core(ctx, step));
+  sgld_kernel<<<1, 32, 0, ctx->stream>>>(ctx->psi_dev, ctx->g_dev, Md, pd, nullptr, eps_t,
+                                         ctx->d + 2, ctx->cfg.seed, step, nullptr,
+                                         ctx->status_dev);
+  CK(cudaGetLastError());
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  ulisse_status r = status_to_result(ctx, st);
+  if (r == ULISSE_ERR_ARG) return r;
+  CK(cudaMemcpyAsync(psi_inout, ctx->psi_dev, sizeof(double) * (ctx->d + 2),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  if (g_out)
+    CK(cudaMemcpyAsync(g_out, ctx->g_dev, sizeof(double) * (ctx->d + 2), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return r;
+}
+
+ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* eps_dev,
+                                int n_steps, const double* M, const double* prior_grad,
+                                unsigned long long step0, double* trace_dev) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!psi_dev || !eps_dev || n_steps < 0) return fail(ctx, ULISSE_ERR_ARG, "bad chain arguments");
+  const int p = ctx->d + 2;
+  const double *Md, *pd;
+  CKS(upload_M_prior(ctx, M, prior_grad, &Md, &pd));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  CK(cudaMemcpyAsync(ctx->psi_dev, psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  for (int k = 0; k < n_steps; ++k) {
+    const unsigned long long step = step0 + (unsigned long long)k;
+    CKS(grad_core(ctx, step));
+    sgld_kernel<<<1, 32, 0, ctx->stream>>>(ctx->psi_dev, ctx->g_dev, Md, pd, eps_dev + k, 0.0, p,
+                                           ctx->cfg.seed, step,
+                                           trace_dev ? trace_dev + (long long)k * p : nullptr,
+                                           ctx->status_dev);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(psi_dev, ctx->psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (mvp_rounds) *mvp_rounds = ctx->mvp_rounds;
+  if (entry_rhs) *entry_rhs = ctx->entry_rhs;
+  return ULISSE_OK;
+}
+
+const char* ulisse_last_error(const ulisse_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+void ulisse_destroy(ulisse_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,
+                   reinterpret_cast<void**>(&ctx->params), reinterpret_cast<void**>(&ctx->psi_dev),
+                   &ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD, &ctx->SE,
+                   reinterpret_cast<void**>(&ctx->st), reinterpret_cast<void**>(&ctx->live),
+                   reinterpret_cast<void**>(&ctx->n_live_dev), reinterpret_cast<void**>(&ctx->iota),
+                   &ctx->partials, reinterpret_cast<void**>(&ctx->counters),
+                   reinterpret_cast<void**>(&ctx->gpart), reinterpret_cast<void**>(&ctx->gcounter),
+                   reinterpret_cast<void**>(&ctx->g_dev), &ctx->sa_dev,
+                   reinterpret_cast<void**>(&ctx->amap), reinterpret_cast<void**>(&ctx->bmap),
+                   reinterpret_cast<void**>(&ctx->M_dev), reinterpret_cast<void**>(&ctx->prior_dev),
+                   reinterpret_cast<void**>(&ctx->status_dev)})
+    dev_free(*p);
+  if (ctx->h_n_live) cudaFreeHost(ctx->h_n_live);
+  if (ctx->h_status) cudaFreeHost(ctx->h_status);
+  delete ctx;
+}
+
+}  // extern "C"

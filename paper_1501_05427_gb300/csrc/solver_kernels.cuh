@@ -1,0 +1,303 @@
+// Vector kernels of the solver path: parameter unpack + prescale, Hutchinson probes,
+// batched CG (Algorithm 1) with the ULISSE truncation and reweighting (Sec. 4), and the
+// SGLD update (Sec. 2.1).  Vectors are T (float or double); every scalar recurrence --
+// e^T e, d^T K d, alpha, beta, the early-stop test and the ULISSE weights -- is FP64.
+#pragma once
+
+#include "ulisse_internal.cuh"
+
+namespace ulisse {
+
+constexpr int kCgNT = 512;
+
+// ------------------------------------------------------------------------------------
+// a1: parameters from psi, and x^ = x / l (rows >= n and dims >= d stay zero).
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void prescale_kernel(const double* __restrict__ psi, const float* __restrict__ X,
+                                T* __restrict__ xhat, long long n, int d, int DP,
+                                DevParams* __restrict__ P) {
+  double inv_l[kMaxD];
+  for (int k = 0; k < d; ++k) inv_l[k] = exp(-psi[k]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int k = 0; k < d + 2; ++k) P->psi[k] = psi[k];
+    for (int k = 0; k < d; ++k) P->inv_l[k] = inv_l[k];
+    const double s2 = exp(psi[d]), lam = exp(psi[d + 1]);
+    P->sigma2 = s2;
+    P->lambda = lam;
+    P->c0f = (float)log2(s2);
+    P->c1f = (float)(0.5 * 1.4426950408889634);  // log2(e) / 2
+    P->lambdaf = (float)lam;
+  }
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    for (int k = 0; k < DP; ++k)
+      xhat[i * DP + k] = (k < d) ? (T)((double)X[i * d + k] * inv_l[k]) : T(0);
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// a2: probes r_j (column j = 1..nr of B): +-1 from the top bit, or N(0,1) by Box-Muller,
+// element i of probe j from Philox counter (i, j, epoch, 1) keyed by (seed, 0).
+// ------------------------------------------------------------------------------------
+template <typename T>
+__global__ void probes_kernel(T* __restrict__ B, long long ld, long long n, int nr, int kind,
+                              unsigned long long seed, unsigned long long epoch) {
+  const int j = blockIdx.y + 1;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    uint64_t w[4];
+    philox4x64_10((uint64_t)i, (uint64_t)j, epoch, kPurposeProbe, seed, 0, w);
+    T v;
+    if (kind == 0) v = (w[0] >> 63) ? T(-1) : T(1);
+    else v = (T)box_muller(w[0], w[1]);
+    B[(long long)j * ld + i] = v;
+  }
+}
+
+template <typename T>
+struct CgArgs {
+  T* S;          // iterates s_m
+  T* E;          // residuals e_m
+  T* D;          // directions d_m
+  const T* KD;   // K d_m (or K s_0 before the first iteration)
+  const T* B;    // right-hand sides
+  T* SE;         // ULISSE estimates
+  long long n, ld;
+  ColState* st;
+  const int* live;
+  double alpha_thr, eps, beta;
+  int max_iter;
+  int has_s0;
+  unsigned long long seed, step;
+  int* status;
+};
+
+// Accepted steps after the early stop: j = 1, 2, ... while u_j < 1/w_j = exp(-beta j).
+__device__ inline int draw_J(unsigned long long seed, unsigned long long step, int colid,
+                             int est, double beta, int jcap) {
+  int J = 0;
+  for (int j = 1; j <= jcap; ++j) {
+    uint64_t w[4];
+    philox4x64_10((uint64_t)j, (uint64_t)colid, step, kPurposeUlisse | ((uint64_t)est << 8),
+                  seed, 0, w);
+    if (u01_53(w[0]) < exp(-beta * (double)j)) J = j;
+    else break;
+  }
+  return J;
+}
+
+// prod_{r=0}^{j} w_r, w_r = exp(beta r).
+__device__ inline double weight_product(int j, double beta) {
+  double W = 1.0;
+  for (int r = 0; r <= j; ++r) W *= exp(beta * (double)r);
+  return W;
+}
+
+// e_0 = b - K s_0, d_0 = e_0, draws of J; one CTA per column.
+template <typename T>
+__global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgNT / 32];
+  const int c = blockIdx.x;
+  ColState& st = a.st[c];
+  T* s = a.S + c * a.ld;
+  T* e = a.E + c * a.ld;
+  T* d = a.D + c * a.ld;
+  const T* b = a.B + c * a.ld;
+  const T* ks0 = a.KD + c * a.ld;
+  double p = 0.0;
+  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
+    if (!a.has_s0) s[i] = T(0);
+    const T ei = a.has_s0 ? b[i] - ks0[i] : b[i];
+    e[i] = ei;
+    d[i] = ei;
+    p += (double)ei * (double)ei;
+  }
+  const double ee = block_sum<kCgNT>(p, red);
+  const int n_est = st.n_est;
+  const bool done = sqrt(ee) < a.eps;
+  if (done) {
+    for (int t = 0; t < n_est; ++t) {
+      T* se = a.SE + (long long)(st.est_off + t) * a.ld;
+      for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st.ee = ee;
+    st.l = 0;
+    st.m = 0;
+    st.outcome = 0;
+    st.J[0] = draw_J(a.seed, a.step, st.colid, 0, a.beta, a.max_iter);
+    st.J[1] = n_est > 1 ? draw_J(a.seed, a.step, st.colid, 1, a.beta, a.max_iter) : -1;
+    st.phase = done ? kDone : kPre;
+  }
+}
+
+// One CG iteration (Algorithm 1) on every live column, with the ULISSE bookkeeping:
+// the increment delta_{m+1} = alpha_m d_m is added with weight prod_{r<=j} w_r to every
+// estimator whose J >= j (j = m+1-l) once the early stop at l has been reached; at l the
+// estimators start from s_l.  One CTA per live column.
+template <typename T>
+__global__ void __launch_bounds__(kCgNT) cg_iter_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgNT / 32];
+  const int c = a.live[blockIdx.x];
+  ColState& st = a.st[c];
+  T* s = a.S + c * a.ld;
+  T* e = a.E + c * a.ld;
+  T* d = a.D + c * a.ld;
+  const T* kd = a.KD + c * a.ld;
+  const double ee = st.ee;
+  const int phase = st.phase, l = st.l, m = st.m, n_est = st.n_est, outcome0 = st.outcome;
+  const int J0 = st.J[0], J1 = st.J[1];
+  T* se0 = a.SE + (long long)st.est_off * a.ld;
+  T* se1 = se0 + a.ld;
+
+  double p = 0.0;
+  for (long long i = threadIdx.x; i < a.n; i += kCgNT) p += (double)d[i] * (double)kd[i];
+  const double dKd = block_sum<kCgNT>(p, red);
+  if (!(dKd > 0.0) || !isfinite(dKd)) {
+    // Breakdown: K is not positive definite along d, or a value is not finite.
+    if (phase == kPre)
+      for (int t = 0; t < n_est; ++t) {
+        T* se = se0 + t * a.ld;
+        for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      st.outcome = 3;
+      st.phase = kDone;
+      atomicOr(a.status, kStatusBreakdown);
+    }
+    return;
+  }
+  const double al = ee / dKd;
+  const T alT = (T)al;
+  T w0 = T(0), w1 = T(0);
+  if (phase == kTail) {
+    const int j = m + 1 - l;
+    const double Wa = weight_product(j, a.beta) * al;
+    if (J0 >= j) w0 = (T)Wa;
+    if (n_est > 1 && J1 >= j) w1 = (T)Wa;
+  }
+  double p2 = 0.0;
+  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
+    const T di = d[i];
+    s[i] = fma(alT, di, s[i]);
+    const T ei = fma(-alT, kd[i], e[i]);
+    e[i] = ei;
+    p2 += (double)ei * (double)ei;
+    if (w0 != T(0)) se0[i] = fma(w0, di, se0[i]);
+    if (w1 != T(0)) se1[i] = fma(w1, di, se1[i]);
+  }
+  const double ee1 = block_sum<kCgNT>(p2, red);
+
+  const int m1 = m + 1;
+  int ph = phase, l1 = l, outcome = outcome0;
+  bool copy_s = false, done = false;
+  const int jmax = (n_est > 1 && J1 > J0) ? J1 : J0;
+  if (ph == kPre && sqrt(ee1) < a.alpha_thr) {
+    l1 = m1;
+    ph = kTail;
+    copy_s = true;
+  }
+  const bool conv = sqrt(ee1) < a.eps;
+  if (ph == kPre && conv) {
+    copy_s = true;
+    done = true;
+  } else if (ph == kTail && (m1 - l1 >= jmax || conv)) {
+    done = true;
+  } else if (m1 >= a.max_iter) {
+    if (ph == kPre) copy_s = true;
+    outcome = 4;
+    done = true;
+  }
+  if (copy_s)
+    for (int t = 0; t < n_est; ++t) {
+      T* se = se0 + t * a.ld;
+      for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
+    }
+  if (!done) {
+    const T btT = (T)(ee1 / ee);
+    for (long long i = threadIdx.x; i < a.n; i += kCgNT) d[i] = fma(btT, d[i], e[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st.ee = ee1;
+    st.m = m1;
+    st.l = l1;
+    st.outcome = outcome;
+    st.phase = done ? kDone : ph;
+    if (outcome == 4) atomicOr(a.status, kStatusMaxIter);
+  }
+}
+
+// Live list of the columns still iterating, in column order; count to *n_live.
+__global__ void compact_kernel(const ColState* __restrict__ st, int R, int* __restrict__ live,
+                               int* __restrict__ n_live) {
+  if (threadIdx.x != 0) return;
+  int k = 0;
+  for (int c = 0; c < R; ++c)
+    if (st[c].phase != kDone) live[k++] = c;
+  *n_live = k;
+}
+
+// ------------------------------------------------------------------------------------
+// a7: SGLD proposal psi' = psi + eps/2 M (g + grad log p) + sqrt(eps) L xi, L L^T = M,
+// xi_k standard normal from Philox counter (k, 0, step, 3).  One thread.
+// ------------------------------------------------------------------------------------
+__global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__ g,
+                            const double* __restrict__ M, const double* __restrict__ prior,
+                            const double* __restrict__ eps_arr, double eps_scalar, int p,
+                            unsigned long long seed, unsigned long long step,
+                            double* __restrict__ trace, int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double Mm[kMaxP * kMaxP], L[kMaxP * kMaxP], xi[kMaxP], v[kMaxP];
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j) Mm[i * p + j] = M ? M[i * p + j] : (i == j ? 1.0 : 0.0);
+  for (int i = 0; i < p * p; ++i) L[i] = 0.0;
+  for (int j = 0; j < p; ++j) {
+    double s = Mm[j * p + j];
+    for (int k = 0; k < j; ++k) s -= L[j * p + k] * L[j * p + k];
+    if (!(s > 0.0)) {
+      atomicOr(status, kStatusBadM);
+      return;
+    }
+    L[j * p + j] = sqrt(s);
+    for (int i = j + 1; i < p; ++i) {
+      double t = Mm[i * p + j];
+      for (int k = 0; k < j; ++k) t -= L[i * p + k] * L[j * p + k];
+      L[i * p + j] = t / L[j * p + j];
+    }
+  }
+  for (int k = 0; k < p; ++k) {
+    uint64_t w[4];
+    philox4x64_10((uint64_t)k, 0, step, kPurposeSgld, seed, 0, w);
+    xi[k] = box_muller(w[0], w[1]);
+  }
+  const double eps = eps_arr ? *eps_arr : eps_scalar;
+  for (int i = 0; i < p; ++i) v[i] = g[i] + (prior ? prior[i] : 0.0);
+  double out[kMaxP];
+  for (int i = 0; i < p; ++i) {
+    double drift = 0.0, noise = 0.0;
+    for (int j = 0; j < p; ++j) drift += Mm[i * p + j] * v[j];
+    for (int j = 0; j <= i; ++j) noise += L[i * p + j] * xi[j];
+    out[i] = psi[i] + 0.5 * eps * drift + sqrt(eps) * noise;
+  }
+  for (int i = 0; i < p; ++i) {
+    psi[i] = out[i];
+    if (trace) trace[i] = out[i];
+  }
+}
+
+// Element-type conversion between caller buffers and the context's (FP64 contexts).
+template <typename S, typename D>
+__global__ void convert_cols_kernel(const S* __restrict__ src, long long lds, D* __restrict__ dst,
+                                    long long ldd, long long n) {
+  const int c = blockIdx.y;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    dst[c * ldd + i] = (D)src[c * lds + i];
+}
+
+}  // namespace ulisse

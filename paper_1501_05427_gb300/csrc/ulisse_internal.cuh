@@ -1,0 +1,235 @@
+// Internal declarations of libulisse: device helpers, shared structs and launchers.
+// Nothing here is part of the public ABI (include/ulisse.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ulisse {
+
+constexpr int kMaxD = 16;
+constexpr int kMaxP = kMaxD + 2;
+constexpr int kBN = 64;          // points per staged j-tile
+constexpr int kStages = 3;       // staged j-tiles in flight per CTA
+constexpr int kMaxRChunk = 32;   // right-hand sides per K V launch
+constexpr int kMaxM = 64;        // rank of the gradient's bilinear form per launch
+
+// Device status bits (OR-ed into the context's status word).
+constexpr int kStatusBreakdown = 1;
+constexpr int kStatusMaxIter = 2;
+constexpr int kStatusTimeout = 4;
+constexpr int kStatusBadM = 8;
+
+// Random-stream purposes (fourth Philox counter word, estimator index in bits 8..15).
+constexpr uint64_t kPurposeProbe = 1;
+constexpr uint64_t kPurposeUlisse = 2;
+constexpr uint64_t kPurposeSgld = 3;
+
+// Scalars derived from psi on the device (written by the prescale kernel).
+struct DevParams {
+  double psi[kMaxP];
+  double inv_l[kMaxD];   // 1 / l_d
+  double sigma2;         // sigma^2
+  double lambda;         // lambda (noise variance)
+  float c0f;             // log2(sigma^2)
+  float c1f;             // log2(e) / 2, so k_s = exp2(c0 - c1 * dist)
+  float lambdaf;
+  float pad;
+};
+
+// Per-column solver state (Algorithm 1 + ULISSE truncation, Sec. 4).
+enum ColPhase { kPre = 0, kTail = 1, kDone = 2 };
+struct ColState {
+  double ee;      // e_m^T e_m
+  int phase;      // ColPhase
+  int l;          // early-stop iteration (0 until reached)
+  int m;          // CG iterations done
+  int outcome;    // 0 ok, 3 breakdown, 4 max_iter
+  int J[2];       // accepted steps after the early stop, per estimator
+  int n_est;      // 1 or 2 estimators
+  int est_off;    // first estimator column in the estimate buffer
+  int colid;      // random-stream column index
+  int pad;
+};
+
+// ------------------------------------------------------------------------------------
+// Philox4x64-10 (Salmon et al., SC'11), from the published round function.
+// ------------------------------------------------------------------------------------
+__host__ __device__ inline void philox4x64_10(uint64_t c0, uint64_t c1, uint64_t c2,
+                                              uint64_t c3, uint64_t k0, uint64_t k1,
+                                              uint64_t out[4]) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+#ifdef __CUDA_ARCH__
+    const uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+    const uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+#else
+    const unsigned __int128 p0 = (unsigned __int128)M0 * c0;
+    const unsigned __int128 p1 = (unsigned __int128)M1 * c2;
+    const uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+    const uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+#endif
+    const uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += W0; k1 += W1;
+  }
+  out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// Uniform on [0,1) from the top 53 bits.
+__host__ __device__ inline double u01_53(uint64_t w) {
+  return (double)(w >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Standard normal from two words (Box-Muller, first of the pair), in double.
+__device__ inline double box_muller(uint64_t w0, uint64_t w1) {
+  const double u1 = u01_53(w0), u2 = u01_53(w1);
+  return sqrt(-2.0 * log(1.0 - u1)) * cos(6.283185307179586 * u2);
+}
+
+// ------------------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA unit) into shared memory, tracked by an mbarrier.
+// ------------------------------------------------------------------------------------
+__device__ inline uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ inline void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ inline void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ inline void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile(
+      "{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(
+          smem_u32(bar)),
+      "r"(bytes)
+      : "memory");
+}
+
+// 1-D bulk copy global -> shared; dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ inline void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ inline bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: about a second at most, then false (the caller reports a timeout).
+__device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 16) __nanosleep(256);
+  }
+  return false;
+}
+
+__device__ inline float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// ------------------------------------------------------------------------------------
+// Block reductions (fixed order: deterministic).
+// ------------------------------------------------------------------------------------
+__device__ inline double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NT>
+__device__ inline double block_sum(double v, double* scratch /* >= NT/32 */) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NT / 32; ++i) t += scratch[i];
+    scratch[0] = t;
+  }
+  __syncthreads();
+  t = scratch[0];
+  __syncthreads();
+  return t;
+}
+
+// ------------------------------------------------------------------------------------
+// Launch descriptors.
+// ------------------------------------------------------------------------------------
+enum KmvMode { kModeK = 0, kModeDLen = 1, kModeDSig = 2 };
+
+struct KmvLaunch {
+  const void* xhat;      // ldn x DP prescaled inputs (x / l), zero padded
+  long long n, ldn;
+  int d, DP;
+  const void* V;         // column c of the operand at V + c * ldv
+  long long ldv;
+  const int* vmap;       // operand columns, R entries
+  int R;                 // right-hand sides (<= kMaxRChunk)
+  void* U;               // result column c at U + c * ldu
+  long long ldu;
+  const int* umap;       // result columns, R entries
+  const DevParams* params;
+  int mode;              // KmvMode
+  int which;             // dimension for kModeDLen
+  void* partials;        // split-j scratch
+  size_t partials_bytes;
+  int* counters;         // one per row block, zero between launches
+  int counters_len;
+  int* status;
+  int num_sms;
+  // Set by the launcher when the scratch above is too small (it then returns
+  // cudaErrorMemoryAllocation without launching).
+  size_t need_partials_bytes;
+  int need_counters;
+};
+
+struct GradLaunch {
+  const void* xhat;
+  long long n, ldn;
+  int d, DP;
+  const void* A;         // left factors: column amap[m] of A, scaled by sa[m]
+  const int* amap;
+  const void* sa;        // device, M scales (element type of A)
+  const void* B;         // right factors: column bmap[m] of B
+  const int* bmap;
+  long long ld;
+  int M;
+  const DevParams* params;
+  double* partials;      // per-CTA FP64 partial sums, kMaxP each
+  size_t partials_len;   // doubles
+  int* counter;          // single counter, zero between launches
+  double* g_out;         // device, d + 2 doubles
+  int* status;
+  int num_sms;
+  size_t need_partials_len;  // set when partials_len is too small
+};
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_kmv_f32(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_f64(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_grad_f32(GradLaunch& L, cudaStream_t s);
+cudaError_t launch_grad_f64(GradLaunch& L, cudaStream_t s);
+
+}  // namespace ulisse

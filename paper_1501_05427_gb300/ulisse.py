@@ -1,0 +1,293 @@
+"""Thin Python binding of libulisse (include/ulisse.h).
+
+Argument marshalling only: every step of the method runs in the library's CUDA kernels.
+PyTorch provides device memory and the stream.  Blocks of vectors are passed as (n, R)
+tensors stored column-major (``t.T.is_contiguous()``); other layouts are copied once into
+that layout.  The library is loaded from ``paper_1501_05427_gb300/_build/libulisse.so``;
+if it is missing, ``load()`` raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libulisse.so")
+
+ULISSE_OK = 0
+ULISSE_ERR_ARG = 1
+ULISSE_ERR_CUDA = 2
+ULISSE_ERR_BREAKDOWN = 3
+ULISSE_ERR_MAXITER = 4
+ULISSE_ERR_NOMEM = 5
+ULISSE_ERR_TIMEOUT = 6
+
+PREC_FP32, PREC_MIXED, PREC_FP64 = 0, 1, 2
+PROBE_RADEMACHER, PROBE_GAUSSIAN = 0, 1
+
+EXPORTED = [
+    "ulisse_config_default", "ulisse_create", "ulisse_create_host", "ulisse_kmv",
+    "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
+    "ulisse_counters", "ulisse_last_error", "ulisse_destroy",
+]
+
+
+class ulisse_config(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("n_probes", ctypes.c_int),
+        ("probe_kind", ctypes.c_int),
+        ("probe_refresh", ctypes.c_int),
+        ("warm_start_probes", ctypes.c_int),
+        ("q", ctypes.c_double),
+        ("beta", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("max_iter", ctypes.c_int),
+        ("seed", ctypes.c_ulonglong),
+    ]
+
+
+class ulisse_col_stats(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int), ("iterations", ctypes.c_int), ("outcome", ctypes.c_int),
+                ("J0", ctypes.c_int), ("J1", ctypes.c_int)]
+
+
+class UlisseError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("ulisse status %d: %s" % (status, msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libulisse.so (built by ``paper_1501_05427_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libulisse.so not built: run __graft_entry__.build() "
+                           "(or python -m paper_1501_05427_gb300.build)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, D, LL, U64 = (ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong,
+                        ctypes.c_ulonglong)
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    cfgp = ctypes.POINTER(ulisse_config)
+    sp = ctypes.POINTER(ulisse_col_stats)
+    lib.ulisse_config_default.argtypes = [cfgp]
+    lib.ulisse_config_default.restype = None
+    lib.ulisse_create.argtypes = [PP, P, P, LL, I, cfgp, P]
+    lib.ulisse_create_host.argtypes = [PP, P, P, LL, I, cfgp, P]
+    lib.ulisse_kmv.argtypes = [P, P, I, P, I, P]
+    lib.ulisse_kmv_f64.argtypes = [P, P, I, P, I, P]
+    lib.ulisse_solve.argtypes = [P, P, P, I, P, P, P, U64, sp]
+    lib.ulisse_grad.argtypes = [P, P, U64, P, sp]
+    lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
+    lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
+    lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D)]
+    lib.ulisse_last_error.argtypes = [P]
+    lib.ulisse_last_error.restype = ctypes.c_char_p
+    lib.ulisse_destroy.argtypes = [P]
+    lib.ulisse_destroy.restype = None
+    for name in EXPORTED:
+        f = getattr(lib, name)
+        if name not in ("ulisse_config_default", "ulisse_last_error", "ulisse_destroy"):
+            f.restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def ulisse_config_default(**overrides) -> ulisse_config:
+    cfg = ulisse_config()
+    load().ulisse_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _f64_host(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.size == n
+    return a
+
+
+def _hptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _colmajor(t):
+    """(n,) or (n, R) CUDA tensor -> (n, R) column-major tensor (copy only if needed)."""
+    if t.dim() == 1:
+        t = t[:, None]
+    if not t.t().is_contiguous():
+        t = t.t().contiguous().t()
+    return t
+
+
+class Context:
+    """One GP regression problem on the current CUDA device (ulisse_create)."""
+
+    def __init__(self, X, y, cfg: ulisse_config | None = None, stream=None, host=False):
+        import torch
+        self._lib = load()
+        cfg = cfg or ulisse_config_default()
+        self.cfg = cfg
+        if host:
+            Xh = np.ascontiguousarray(X, dtype=np.float32)
+            yh = np.ascontiguousarray(y, dtype=np.float32)
+            n, d = Xh.shape
+            self._keep = (Xh, yh)
+            xp, yp = _hptr(Xh), _hptr(yh)
+        else:
+            X = X.contiguous().float()
+            y = y.contiguous().float()
+            n, d = X.shape
+            self._keep = (X, y)
+            xp, yp = ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(y.data_ptr())
+        self.n, self.d, self.p = n, d, d + 2
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        fn = self._lib.ulisse_create_host if host else self._lib.ulisse_create
+        st = fn(ctypes.byref(h), xp, yp, n, d, ctypes.byref(cfg),
+                ctypes.c_void_p(self.stream.cuda_stream))
+        if st != ULISSE_OK:
+            raise UlisseError(st, self._lib.ulisse_last_error(None).decode())
+        self._h = h
+
+    # -- helpers ---------------------------------------------------------------------
+    def _check(self, st, allow=()):
+        if st != ULISSE_OK and st not in allow:
+            raise UlisseError(st, self._lib.ulisse_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.ulisse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- API ---------------------------------------------------------------------------
+    def kmv(self, psi, V, which=-1, out=None):
+        """U = K V (which=-1) or dK/dpsi_which V.  V: (n,) or (n, R) CUDA tensor."""
+        import torch
+        f64 = V.dtype == torch.float64
+        Vc = _colmajor(V)
+        R = Vc.shape[1]
+        if out is None:
+            out = torch.empty((R, self.n), dtype=V.dtype, device=V.device).t()
+        psi = _f64_host(psi, self.p)
+        fn = self._lib.ulisse_kmv_f64 if f64 else self._lib.ulisse_kmv
+        self._check(fn(self._h, _hptr(psi), which, ctypes.c_void_p(Vc.data_ptr()), R,
+                       ctypes.c_void_p(out.data_ptr())))
+        return out[:, 0] if V.dim() == 1 else out
+
+    def solve(self, psi, B, n_est=None, S0=None, step=0, allow=()):
+        """ULISSE estimates of K^{-1} B.  Returns (S_est (n, sum n_est), stats list)."""
+        import torch
+        Bc = _colmajor(B.float())
+        R = Bc.shape[1]
+        ne = np.ascontiguousarray(n_est if n_est is not None else np.ones(R), dtype=np.int32)
+        tot = int(ne.sum())
+        S_est = torch.empty((tot, self.n), dtype=torch.float32, device=B.device).t()
+        S0c = _colmajor(S0.float()) if S0 is not None else None
+        stats = (ulisse_col_stats * R)()
+        psi = _f64_host(psi, self.p)
+        st = self._lib.ulisse_solve(self._h, _hptr(psi), ctypes.c_void_p(Bc.data_ptr()), R,
+                                    _hptr(ne), ctypes.c_void_p(S0c.data_ptr()) if S0c is not None
+                                    else None, ctypes.c_void_p(S_est.data_ptr()), step, stats)
+        self._check(st, allow)
+        return S_est, [(s.l, s.iterations, s.outcome, s.J0, s.J1) for s in stats]
+
+    def grad(self, psi, step=0, allow=()):
+        """Unbiased gradient estimate (host numpy, p) and per-column stats."""
+        psi = _f64_host(psi, self.p)
+        g = np.zeros(self.p)
+        R = 1 + self.cfg.n_probes
+        stats = (ulisse_col_stats * R)()
+        st = self._lib.ulisse_grad(self._h, _hptr(psi), step, _hptr(g), stats)
+        self._check(st, allow)
+        return g, [(s.l, s.iterations, s.outcome, s.J0, s.J1) for s in stats]
+
+    def sgld_step(self, psi, eps_t, step, M=None, prior_grad=None, allow=()):
+        """One SGLD step; returns (psi_new, g) as numpy arrays."""
+        psi = np.array(psi, dtype=np.float64, copy=True)
+        g = np.zeros(self.p)
+        Mh = np.ascontiguousarray(M, dtype=np.float64) if M is not None else None
+        ph = _f64_host(prior_grad, self.p) if prior_grad is not None else None
+        st = self._lib.ulisse_sgld_step(self._h, _hptr(psi), float(eps_t), _hptr(Mh), _hptr(ph),
+                                        step, _hptr(g))
+        self._check(st, allow)
+        return psi, g
+
+    def sgld_chain(self, psi_dev, eps_dev, step0=0, M=None, prior_grad=None, trace_dev=None,
+                   allow=()):
+        """len(eps_dev) SGLD steps with psi resident on the device (in place)."""
+        Mh = np.ascontiguousarray(M, dtype=np.float64) if M is not None else None
+        ph = _f64_host(prior_grad, self.p) if prior_grad is not None else None
+        st = self._lib.ulisse_sgld_chain(
+            self._h, ctypes.c_void_p(psi_dev.data_ptr()), ctypes.c_void_p(eps_dev.data_ptr()),
+            int(eps_dev.numel()), _hptr(Mh), _hptr(ph), step0,
+            ctypes.c_void_p(trace_dev.data_ptr()) if trace_dev is not None else None)
+        self._check(st, allow)
+        return psi_dev
+
+    def counters(self):
+        a = ctypes.c_longlong()
+        b = ctypes.c_double()
+        self._lib.ulisse_counters(self._h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value
+
+
+# Same names as the C ABI, for callers that prefer functions over the class.
+def ulisse_create(X, y, cfg=None, stream=None):
+    return Context(X, y, cfg, stream)
+
+
+def ulisse_create_host(X, y, cfg=None, stream=None):
+    return Context(X, y, cfg, stream, host=True)
+
+
+def ulisse_kmv(ctx: Context, psi, which, V):
+    return ctx.kmv(psi, V, which)
+
+
+ulisse_kmv_f64 = ulisse_kmv
+
+
+def ulisse_solve(ctx: Context, psi, B, n_est=None, S0=None, step=0):
+    return ctx.solve(psi, B, n_est, S0, step)
+
+
+def ulisse_grad(ctx: Context, psi, step=0):
+    return ctx.grad(psi, step)
+
+
+def ulisse_sgld_step(ctx: Context, psi, eps_t, step, M=None, prior_grad=None):
+    return ctx.sgld_step(psi, eps_t, step, M, prior_grad)
+
+
+def ulisse_sgld_chain(ctx: Context, psi_dev, eps_dev, step0=0, M=None, prior_grad=None,
+                      trace_dev=None):
+    return ctx.sgld_chain(psi_dev, eps_dev, step0, M, prior_grad, trace_dev)
+
+
+def ulisse_counters(ctx: Context):
+    return ctx.counters()
+
+
+def ulisse_destroy(ctx: Context):
+    ctx.close()

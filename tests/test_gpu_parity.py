@@ -1,0 +1,347 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the same seeded
+inputs.
+
+Tolerances (derivation in the design notes):
+  * K V, FP32 path: every entry within 1e-5 of its own dot-product scale sum_j |A_ij||V_jr|
+    (the standard rounding bound of a length-n dot product evaluated in FP32 with an
+    approximate exp), and 1e-5 in Frobenius norm relative to the exact product.
+  * K V, FP64 path: 1e-12 of the same scale.
+  * Seeded ULISSE solves: identical integer outcomes (early-stop iteration l, accepted steps
+    J, iterations) unless the oracle's early-stop test is within 1e-4 of the threshold;
+    estimates within 1e-4 (FP32 path) or 1e-6 (FP64 path, float output buffer) per column.
+  * Seeded gradients: ||g_gpu - g_oracle|| <= 1e-4 ||g_oracle|| (FP32), 1e-9 (FP64).
+  * FP32 seeded parity is checked where the CG trajectories are short (Census-shaped
+    inputs, n <= 2000): FP32 products make a CG trajectory drift from the FP64 one
+    geometrically with the iteration count (about 1e-5 after 10 iterations, 1e-2 after 20
+    on these inputs), so longer FP32 runs are checked statistically (unbiasedness) and
+    the FP64 path is checked seeded on the ill-conditioned, long-trajectory problems.
+"""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU runs deselect this module
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1501_05427_gb300 import ulisse as u  # noqa: E402
+from paper_1501_05427_gb300 import workloads as w  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
+def _ctx(prob, **cfg):
+    X = torch.from_numpy(prob.X).cuda()
+    y = torch.from_numpy(prob.y).cuda()
+    return u.Context(X, y, u.ulisse_config_default(**cfg))
+
+
+def _kv_check(U, ref, scale, tol):
+    err = np.abs(U - ref)
+    assert np.all(err <= tol * scale + 1e-30), float(np.max(err / (scale + 1e-300)))
+    assert np.linalg.norm(U - ref) <= tol * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------------------------------
+# K V (Sec. 3)
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("n,d,R", [(1, 1, 1), (37, 2, 3), (64, 3, 1), (1000, 2, 5),
+                                   (1333, 8, 17), (2111, 16, 7), (3000, 5, 32), (700, 4, 40)])
+def test_kmv_fp32(orc, n, d, R):
+    prob = w.random_problem(n, d, seed=100 + n + d)
+    rng = np.random.default_rng(n * R)
+    V = rng.standard_normal((n, R)).astype(np.float32)
+    Xd = prob.X.astype(np.float64)
+    Vd = V.astype(np.float64)
+    with _ctx(prob) as ctx:
+        Vt = torch.from_numpy(V).cuda()
+        for which in [-1] + list(range(d + 2)):
+            Ug = ctx.kmv(prob.psi_true, Vt, which).cpu().numpy().astype(np.float64)
+            A = orc.cov_matrix(Xd, prob.psi_true, which)
+            ref = A @ Vd if n <= 1500 else orc.kmv(Xd, prob.psi_true, Vd, which)
+            scale = np.abs(A) @ np.abs(Vd)
+            _kv_check(Ug, ref, scale, 1e-5)
+
+
+def test_kmv_fp64(orc):
+    prob = w.random_problem(777, 2, seed=5)
+    V = np.random.default_rng(1).standard_normal((777, 5))
+    with _ctx(prob, precision=u.PREC_FP64) as ctx:
+        Vt = torch.from_numpy(V).cuda()
+        for which in (-1, 0, 1, 2, 3):
+            Ug = ctx.kmv(prob.psi_true, Vt, which).cpu().numpy()
+            A = orc.cov_matrix(prob.X.astype(np.float64), prob.psi_true, which)
+            _kv_check(Ug, A @ V, np.abs(A) @ np.abs(V), 1e-12)
+
+
+def test_kmv_full_size_sampled_rows(orc):
+    """Full-size Census-like product (n = 50,000, d = 8, R = 17) in the launch configuration
+    of the benchmark: sampled rows against the oracle, which evaluates them one by one."""
+    prob = w.census_like()
+    n = prob.n
+    rng = np.random.default_rng(3)
+    V = rng.choice([-1.0, 1.0], (n, 17)).astype(np.float32)
+    V[:, 0] = prob.y
+    rows = np.sort(rng.choice(n, 48, replace=False))
+    rows[-1] = n - 1
+    with _ctx(prob, n_probes=16) as ctx:
+        Ug = ctx.kmv(prob.psi_true, torch.from_numpy(V).cuda()).cpu().numpy()[rows]
+    Xd, Vd = prob.X.astype(np.float64), V.astype(np.float64)
+    ref = orc.kmv_rows(Xd, prob.psi_true, Vd, rows)
+    scale = orc.kmv_rows(Xd, prob.psi_true, Vd, rows, absolute=True)
+    _kv_check(Ug.astype(np.float64), ref, scale, 1e-5)
+
+
+def test_kmv_symmetry_and_linearity():
+    """Properties that hold at any size: e_i^T K e_j = e_j^T K e_i; K (aV) = a K V."""
+    prob = w.random_problem(5000, 4, seed=9)
+    with _ctx(prob) as ctx:
+        idx = [0, 17, 2500, 4999]
+        E = torch.zeros((5000, 4), device="cuda")
+        for c, i in enumerate(idx):
+            E[i, c] = 1.0
+        KE = ctx.kmv(prob.psi_true, E).cpu().numpy()
+        S = KE[idx, :]
+        assert np.allclose(S, S.T, rtol=1e-6, atol=0)
+        V = torch.randn((5000, 3), device="cuda")
+        a = ctx.kmv(prob.psi_true, V)
+        b = ctx.kmv(prob.psi_true, 2.0 * V)
+        assert torch.allclose(2.0 * a, b, rtol=1e-6, atol=1e-6)
+
+
+# ----------------------------------------------------------------------------------------
+# ULISSE solves (Sec. 4) and gradients (Eq. gradient:unbiased)
+# ----------------------------------------------------------------------------------------
+def _early_stop_margin(orc, Xd, psi, b, q, iters):
+    """Smallest relative distance of ||e_i|| (i = 1..iters) to the threshold q sqrt(n)."""
+    tr = orc.cg_record(Xd, psi, b, eps=1e-8, max_iter=max(iters, 1) + 1)
+    a = q * math.sqrt(len(b))
+    norms = np.linalg.norm(tr["E"], axis=1)[1:iters + 1]
+    return float(np.min(np.abs(norms - a) / a)) if len(norms) else 1.0
+
+
+def _compare_solves(orc, prob, B, n_est, Sg, st, Sref, st_ref, q, tol):
+    Xd = prob.X.astype(np.float64)
+    R = B.shape[1]
+    col = 0
+    checked = 0
+    for c in range(R):
+        if tuple(st[c][:4]) != tuple(int(v) for v in st_ref[c, :4]):
+            # only allowed where the oracle's early-stop test is within rounding of alpha
+            margin = _early_stop_margin(orc, Xd, prob.psi_true, B[:, c].astype(np.float64), q,
+                                        int(st_ref[c, 1]))
+            assert margin < 1e-4, (c, st[c], st_ref[c], margin)
+            col += n_est[c]
+            continue
+        if n_est[c] > 1:
+            assert st[c][4] == st_ref[c, 4]
+        for t in range(n_est[c]):
+            ref = Sref[:, col + t]
+            err = np.linalg.norm(Sg[:, col + t] - ref) / np.linalg.norm(ref)
+            assert err <= tol, (c, t, err)
+        checked += 1
+        col += n_est[c]
+    assert checked >= R - 1
+
+
+@pytest.mark.parametrize("n,d,R,q", [(700, 8, 4, 1.0), (1500, 8, 9, 1.0), (1800, 8, 6, 1.0),
+                                     (1900, 8, 17, 0.8)])
+def test_solve_parity_fp32(orc, n, d, R, q):
+    """FP32 path on Census-shaped inputs, where the solves stop within a few iterations."""
+    prob = w.census_like(n=n, d=d, seed=300 + n)
+    rng = np.random.default_rng(n)
+    B = rng.choice([-1.0, 1.0], (n, R)).astype(np.float32)
+    B[:, 0] = prob.y
+    n_est = np.ones(R, np.int32)
+    n_est[0] = 2
+    Sref, st_ref = orc.ulisse_solve(prob.X.astype(np.float64), prob.psi_true,
+                                    B.astype(np.float64), n_est=n_est, q=q, beta=1.0, eps=1e-8,
+                                    max_iter=500, seed=21, step=4)
+    assert st_ref[:, 1].max() <= 8       # short trajectories: the FP32 regime
+    with _ctx(prob, q=q, max_iter=500, seed=21) as ctx:
+        Sg, st = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(), n_est=n_est, step=4)
+    _compare_solves(orc, prob, B, n_est, Sg.cpu().numpy().astype(np.float64), st, Sref, st_ref,
+                    q, 1e-4)
+
+
+@pytest.mark.parametrize("n,d,R,q", [(500, 2, 4, 1.0), (1500, 3, 9, 0.6), (2100, 8, 6, 1.0),
+                                     (1000, 2, 5, 1.0)])
+def test_solve_parity_fp64(orc, n, d, R, q):
+    """FP64 path on ill-conditioned inputs (U[0,1]^d, long trajectories): the GPU follows
+    the oracle's CG trajectory to the float resolution of the output buffer."""
+    prob = w.random_problem(n, d, seed=300 + n) if n != 1000 else w.small_2d(n)
+    rng = np.random.default_rng(n)
+    B = rng.choice([-1.0, 1.0], (n, R)).astype(np.float32)
+    B[:, 0] = prob.y
+    n_est = np.ones(R, np.int32)
+    n_est[0] = 2
+    Sref, st_ref = orc.ulisse_solve(prob.X.astype(np.float64), prob.psi_true,
+                                    B.astype(np.float64), n_est=n_est, q=q, beta=1.0, eps=1e-8,
+                                    max_iter=500, seed=21, step=4)
+    with _ctx(prob, precision=u.PREC_FP64, q=q, max_iter=500, seed=21) as ctx:
+        Sg, st = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(), n_est=n_est, step=4)
+    _compare_solves(orc, prob, B, n_est, Sg.cpu().numpy().astype(np.float64), st, Sref, st_ref,
+                    q, 1e-6)
+
+
+def test_solve_fp64_matches_oracle_tightly(orc):
+    prob = w.small_2d(n=400)
+    B = np.random.default_rng(2).standard_normal((400, 3)).astype(np.float32)
+    B[:, 0] = prob.y
+    Sref, st_ref = orc.ulisse_solve(prob.X.astype(np.float64), prob.psi_true,
+                                    B.astype(np.float64), q=1.0, max_iter=300, seed=5, step=1)
+    with _ctx(prob, precision=u.PREC_FP64, max_iter=300, seed=5) as ctx:
+        Sg, st = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(), step=1)
+    for c in range(3):
+        assert tuple(st[c][:4]) == tuple(int(v) for v in st_ref[c, :4])
+    Sg = Sg.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(Sg - Sref)) <= 1e-6 * np.max(np.abs(Sref))
+
+
+def _grad_case(orc, prob, nr, kind, precision, tol, steps=(0, 1, 2), seed=33):
+    n = prob.n
+    Xd, yd = prob.X.astype(np.float64), prob.y.astype(np.float64)
+    with _ctx(prob, n_probes=nr, probe_kind=kind, max_iter=500, seed=seed,
+              precision=precision) as ctx:
+        for step in steps:
+            gref, st_ref = orc.grad_estimate(Xd, yd, prob.psi_true, nr=nr, probe_kind=kind,
+                                             q=1.0, beta=1.0, max_iter=500, seed=seed, step=step)
+            g, st = ctx.grad(prob.psi_true, step=step)
+            same = all(tuple(st[c][:4]) == tuple(int(v) for v in st_ref[c, :4])
+                       for c in range(1 + nr))
+            if not same:
+                B = np.column_stack([yd, orc.probes(n, nr, kind, seed, step)])
+                margins = [_early_stop_margin(orc, Xd, prob.psi_true, B[:, c], 1.0,
+                                              int(st_ref[c, 1])) for c in range(1 + nr)]
+                assert min(margins) < 1e-4, (st, st_ref)
+                continue
+            rel = np.linalg.norm(g - gref) / np.linalg.norm(gref)
+            assert rel <= tol, (step, g, gref, rel)
+
+
+@pytest.mark.parametrize("n,d,nr", [(800, 8, 4), (1700, 8, 8), (1200, 8, 16), (2000, 8, 16)])
+def test_grad_parity_fp32(orc, n, d, nr):
+    _grad_case(orc, w.census_like(n=n, d=d, seed=500 + n), nr, 0, u.PREC_FP32, 1e-4)
+
+
+@pytest.mark.parametrize("n,d,nr,kind", [(800, 2, 4, 0), (1700, 4, 8, 0), (900, 2, 4, 1)])
+def test_grad_parity_fp64(orc, n, d, nr, kind):
+    _grad_case(orc, w.random_problem(n, d, seed=500 + n), nr, kind, u.PREC_FP64, 1e-9)
+
+
+def test_grad_parity_small_2d_fp64(orc):
+    """The 2-D workload's configuration: FP64, 4 Gaussian probes."""
+    _grad_case(orc, w.small_2d(n=1000), 4, 1, u.PREC_FP64, 1e-9, steps=(0, 1))
+
+
+def test_sgld_step_parity(orc):
+    """Three SGLD steps of the 2-D workload (FP64, Gaussian probes, preconditioner, prior)."""
+    prob = w.small_2d(n=600)
+    Xd, yd = prob.X.astype(np.float64), prob.y.astype(np.float64)
+    M = np.diag([0.5, 0.7, 0.9, 1.1])
+    pg = np.array([0.1, -0.2, 0.05, 0.0])
+    with _ctx(prob, n_probes=4, probe_kind=1, max_iter=500, seed=8,
+              precision=u.PREC_FP64) as ctx:
+        psi = prob.psi_true.copy()
+        psi_ref = psi.copy()
+        for step in range(3):
+            psi, g = ctx.sgld_step(psi, 1e-3, step, M=M, prior_grad=pg)
+            psi_ref, gref, _ = orc.sgld_step(Xd, yd, psi_ref, 1e-3, nr=4, probe_kind=1,
+                                             max_iter=500, seed=8, step=step, M=M, prior_grad=pg)
+            assert np.linalg.norm(g - gref) <= 1e-9 * np.linalg.norm(gref)
+            assert np.max(np.abs(psi - psi_ref)) < 1e-12
+
+
+def test_sgld_step_parity_fp32(orc):
+    prob = w.census_like(n=1500, seed=44)
+    Xd, yd = prob.X.astype(np.float64), prob.y.astype(np.float64)
+    with _ctx(prob, n_probes=8, max_iter=500, seed=9) as ctx:
+        psi, g = ctx.sgld_step(prob.psi_true, 1e-4, 0)
+    psi_ref, gref, st_ref = orc.sgld_step(Xd, yd, prob.psi_true, 1e-4, nr=8, max_iter=500,
+                                          seed=9, step=0)
+    assert np.linalg.norm(g - gref) <= 1e-4 * np.linalg.norm(gref)
+    assert np.max(np.abs(psi - psi_ref)) < 1e-6
+
+
+def test_grad_unbiased_fp32_gpu(orc):
+    """E[g~] = g for the FP32 GPU path: the mean of 4000 seeded GPU estimates is within
+    4 standard errors of the exact (Cholesky) gradient -- a check that holds however long
+    the CG trajectories are."""
+    prob = w.census_like(n=600, seed=61)
+    g_exact = orc.exact_gradient(prob.X.astype(np.float64), prob.y.astype(np.float64),
+                                 prob.psi_true)
+    N = 4000
+    with _ctx(prob, n_probes=2, q=0.7, max_iter=600, seed=123) as ctx:
+        G = np.array([ctx.grad(prob.psi_true, step=s)[0] for s in range(N)])
+    se = G.std(axis=0, ddof=1) / math.sqrt(N)
+    z = (G.mean(axis=0) - g_exact) / se
+    assert np.max(np.abs(z)) < 4.0, (G.mean(axis=0), g_exact, se)
+
+
+def test_chain_matches_steps(orc):
+    """The device-resident chain gives the same psi as repeated host-driven steps."""
+    prob = w.random_problem(700, 2, seed=71)
+    eps = torch.full((4,), 2e-3, dtype=torch.float64, device="cuda")
+    with _ctx(prob, n_probes=3, seed=2) as ctx:
+        psi_dev = torch.tensor(prob.psi_true, dtype=torch.float64, device="cuda")
+        trace = torch.zeros((4, 4), dtype=torch.float64, device="cuda")
+        ctx.sgld_chain(psi_dev, eps, step0=10, trace_dev=trace)
+        psi = prob.psi_true.copy()
+        for k in range(4):
+            psi, _ = ctx.sgld_step(psi, 2e-3, 10 + k)
+            assert np.allclose(trace[k].cpu().numpy(), psi, rtol=0, atol=1e-12)
+        assert np.allclose(psi_dev.cpu().numpy(), psi, rtol=0, atol=1e-12)
+
+
+def test_deterministic_repeat():
+    prob = w.random_problem(1100, 3, seed=12)
+    with _ctx(prob, n_probes=4, seed=3) as ctx:
+        g1, _ = ctx.grad(prob.psi_true, step=5)
+        g2, _ = ctx.grad(prob.psi_true, step=5)
+        g3, _ = ctx.grad(prob.psi_true, step=6)
+    assert np.array_equal(g1, g2)
+    assert not np.array_equal(g1, g3)
+
+
+# ----------------------------------------------------------------------------------------
+# Failure reporting (no GPU fault: bad data is caught by the solver's own checks)
+# ----------------------------------------------------------------------------------------
+def test_nan_input_reports_breakdown():
+    prob = w.random_problem(300, 2, seed=1)
+    B = np.random.default_rng(0).standard_normal((300, 2)).astype(np.float32)
+    B[5, 1] = np.nan
+    with _ctx(prob) as ctx:
+        S, st = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(),
+                          allow=(u.ULISSE_ERR_BREAKDOWN,))
+        assert st[1][2] == u.ULISSE_ERR_BREAKDOWN
+        assert st[0][2] == 0
+        # the context stays usable
+        g, _ = ctx.grad(prob.psi_true, step=0)
+        assert np.all(np.isfinite(g))
+
+
+def test_max_iter_reported():
+    prob = w.random_problem(400, 2, seed=2)
+    B = np.random.default_rng(0).standard_normal((400, 1)).astype(np.float32)
+    with _ctx(prob, q=0.0, max_iter=2) as ctx:
+        with pytest.raises(u.UlisseError) as ei:
+            ctx.solve(prob.psi_true, torch.from_numpy(B).cuda())
+        assert ei.value.status == u.ULISSE_ERR_MAXITER
+
+
+def test_bad_psi_rejected():
+    prob = w.random_problem(100, 2, seed=3)
+    with _ctx(prob) as ctx:
+        with pytest.raises(u.UlisseError) as ei:
+            ctx.grad(np.array([0.0, np.nan, 0.0, 0.0]))
+        assert ei.value.status == u.ULISSE_ERR_ARG
+        with pytest.raises(u.UlisseError):
+            ctx.kmv(prob.psi_true, torch.zeros((100, 1), device="cuda"), which=9)

@@ -12,7 +12,8 @@ a wrong sign or index, a transposed operand, a wrong weight) fails at least one 
                         symmetry, positive definiteness (eigvalsh >= lambda)
   cov_matrix(which)     central finite differences of K in psi; dK/dlog lambda = lambda I;
                         dK/dlog sigma^2 = K - lambda I
-  kmv / dkmv_all        dense matrix product with numpy on tiny and ragged sizes
+  kmv / dkmv_all /      dense matrix product with numpy on tiny and ragged sizes
+  kmv_rows
   exact_gradient        central finite differences of the log marginal likelihood
   log_marginal_lik.     scipy.stats.multivariate_normal.logpdf
   cg_record             Cholesky solution (Sec. 3 error definition), conjugacy and residual
@@ -168,6 +169,19 @@ def test_kmv_vs_dense(orc, n, d, R):
     for q in range(d + 2):
         dense = orc.cov_matrix(X, psi, q) @ V
         assert np.max(np.abs(allp[q] - dense)) <= 1e-12 * max(1.0, np.max(np.abs(dense)))
+
+
+def test_kmv_rows_vs_dense(orc):
+    n, d, R = 83, 3, 3
+    X = _rand_X(n, d, 40)
+    psi = np.log([0.4, 0.6, 0.5, 1.1, 0.2])
+    V = np.random.default_rng(40).standard_normal((n, R))
+    rows = [0, 5, 41, 82]
+    for which in (-1, 1, 3, 4):
+        A = orc.cov_matrix(X, psi, which)
+        assert np.max(np.abs(orc.kmv_rows(X, psi, V, rows, which) - (A @ V)[rows])) < 1e-12
+        absu = orc.kmv_rows(X, psi, V, rows, which, absolute=True)
+        assert np.max(np.abs(absu - (np.abs(A) @ np.abs(V))[rows])) < 1e-12
 
 
 # ----------------------------------------------------------------------------------------
