@@ -186,10 +186,34 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx *ctx, double *psi_dev, const double *
                                 int n_steps, const double *M, const double *prior_grad,
                                 unsigned long long step0, double *trace_dev);
 
-/* Number of K V products (one per CG iteration of the batched solve, all live columns at
- * once) and of generated kernel entries times right-hand sides since creation. */
+/* Work counters since creation (each output pointer may be NULL):
+ *   mvp_rounds        K V products issued by the solver (one per batched CG iteration,
+ *                     covering every live column at once),
+ *   entry_rhs         generated covariance entries times right-hand sides (K V and the
+ *                     gradient pass: n^2 R per product),
+ *   kernel_launches   CUDA kernels this library launched. */
 ulisse_status ulisse_counters(const ulisse_ctx *ctx, long long *mvp_rounds,
-                              double *entry_rhs);
+                              double *entry_rhs, long long *kernel_launches);
+
+/* Device-time accounting of the two O(n^2) kernels, from CUDA events recorded on the
+ * context's stream around every launch while enabled.  Algorithmic FLOPs per launch:
+ *   K V:       n^2 (3d + 2 + 2R)   (d differences and d squares-and-adds, the exponent's
+ *                                   FMA and exp, R multiply-adds; the exp counted as 1)
+ *   gradient:  n^2 (5d + 4 + 2M)   (M = 1 + N_r rank of the bilinear form) */
+typedef struct {
+    long long kmv_launches;
+    double kmv_ms;
+    double kmv_flop;
+    long long grad_launches;
+    double grad_ms;
+    double grad_flop;
+} ulisse_profile;
+
+/* Enable (1) or disable (0) the event timing above; enabling resets the totals. */
+ulisse_status ulisse_profile_enable(ulisse_ctx *ctx, int enable);
+
+/* Totals since enabling (synchronises the stream); reset != 0 clears them afterwards. */
+ulisse_status ulisse_profile_read(ulisse_ctx *ctx, ulisse_profile *out, int reset);
 
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);

@@ -64,6 +64,7 @@ def _load():
             lib.orc_dkmv_all.argtypes = [P, L, I, P, P, I, P]
             lib.orc_kmv_rows.argtypes = [P, L, I, P, I, P, I, P, L, P]
             lib.orc_kmv_rows_abs.argtypes = [P, L, I, P, I, P, I, P, L, P]
+            lib.orc_dkmv_all_rows.argtypes = [P, L, I, P, P, I, P, L, P]
             lib.orc_probes.argtypes = [L, I, I, U64, U64, P]
             lib.orc_draw_J.argtypes = [U64, U64, U64, I, D, I]
             lib.orc_draw_J.restype = I
@@ -170,6 +171,30 @@ def kmv_rows(X, psi, V, rows, which=-1, absolute=False):
     fn = _load().orc_kmv_rows_abs if absolute else _load().orc_kmv_rows
     fn(_ptr(X), n, d, _ptr(psi), which, _ptr(Vc), R, _ptr(rows), len(rows), _ptr(U))
     return U.T.copy()
+
+
+def dkmv_all_rows(X, psi, V, rows):
+    """Rows `rows` of all p derivative products, returned as (p, len(rows), R)."""
+    X = _f64(X)
+    n, d = X.shape
+    psi = _f64(psi)
+    Vc, R = _colmajor(V, n)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    U = np.zeros((d + 2, R, len(rows)))
+    _load().orc_dkmv_all_rows(_ptr(X), n, d, _ptr(psi), _ptr(Vc), R, _ptr(rows), len(rows),
+                              _ptr(U))
+    return np.transpose(U, (0, 2, 1)).copy()
+
+
+def omp_threads():
+    """Threads the oracle's OpenMP loops use."""
+    lib = _load()
+    try:
+        f = lib.omp_get_max_threads
+        f.restype = ctypes.c_int
+        return int(f())
+    except AttributeError:
+        return os.cpu_count() or 1
 
 
 def dkmv_all(X, psi, V):

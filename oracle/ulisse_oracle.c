@@ -196,6 +196,34 @@ void orc_kmv_rows_abs(const double *X, long n, int d, const double *psi, int whi
     }
 }
 
+/* All p derivative products restricted to the listed output rows:
+ * U_all[(q*R + r)*nrows + k] = sum_j dK/dpsi_q[rows[k], j] V[j, r]. */
+void orc_dkmv_all_rows(const double *X, long n, int d, const double *psi, const double *V,
+                       int R, const long *rows, long nrows, double *U_all)
+{
+    orc_theta t = unpack(psi, d);
+    const int p = d + 2;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (long k = 0; k < nrows; ++k) {
+        const long i = rows[k];
+        const double *xi = X + i * d;
+        for (int q = 0; q < p; ++q)
+            for (int r = 0; r < R; ++r) U_all[((long)q * R + r) * nrows + k] = 0.0;
+        for (long j = 0; j < n; ++j) {
+            const double *xj = X + j * d;
+            double ks = k_signal(xi, xj, &t);
+            for (int q = 0; q < d; ++q) {
+                double diff = xi[q] - xj[q];
+                double a = ks * diff * diff * t.inv_l2[q];
+                for (int r = 0; r < R; ++r) U_all[((long)q * R + r) * nrows + k] += a * V[(long)r * n + j];
+            }
+            for (int r = 0; r < R; ++r) U_all[((long)d * R + r) * nrows + k] += ks * V[(long)r * n + j];
+            if (i == j)
+                for (int r = 0; r < R; ++r) U_all[((long)(d + 1) * R + r) * nrows + k] += t.lambda * V[(long)r * n + j];
+        }
+    }
+}
+
 /* All p derivative products in one sweep over the entries:
  * U_all[q] (n x R, col-major, q = 0..p-1) = dK/dpsi_q V. */
 void orc_dkmv_all(const double *X, long n, int d, const double *psi,

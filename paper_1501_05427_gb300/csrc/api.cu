@@ -57,7 +57,15 @@ struct ulisse_ctx {
 
   long long mvp_rounds = 0;
   double entry_rhs = 0.0;
+  long long launches = 0;
   std::string err;
+
+  // event timing of the O(n^2) kernels (ulisse_profile_enable)
+  bool prof = false;
+  struct Pending { int kind; cudaEvent_t a, b; double flop; };
+  std::vector<Pending> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> free_events;
+  ulisse_profile totals{};
 };
 
 static thread_local std::string g_create_error;
@@ -81,6 +89,46 @@ static ulisse_status fail(ulisse_ctx* ctx, ulisse_status s, const std::string& m
   if (ctx) ctx->err = msg;
   else g_create_error = msg;
   return s;
+}
+
+// Events around one O(n^2) kernel launch (kind 0: K V, 1: gradient).
+static void prof_begin(ulisse_ctx* ctx, cudaEvent_t* a, cudaEvent_t* b) {
+  if (!ctx->prof) return;
+  if (ctx->free_events.empty()) {
+    cudaEvent_t x, y;
+    cudaEventCreate(&x);
+    cudaEventCreate(&y);
+    ctx->free_events.push_back({x, y});
+  }
+  *a = ctx->free_events.back().first;
+  *b = ctx->free_events.back().second;
+  ctx->free_events.pop_back();
+  cudaEventRecord(*a, ctx->stream);
+}
+
+static void prof_end(ulisse_ctx* ctx, int kind, cudaEvent_t a, cudaEvent_t b, double flop) {
+  if (!ctx->prof) return;
+  cudaEventRecord(b, ctx->stream);
+  ctx->pending.push_back({kind, a, b, flop});
+}
+
+// Fold completed event pairs into the totals (call after a stream synchronisation).
+static void prof_drain(ulisse_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    if (p.kind == 0) {
+      ctx->totals.kmv_launches++;
+      ctx->totals.kmv_ms += ms;
+      ctx->totals.kmv_flop += p.flop;
+    } else {
+      ctx->totals.grad_launches++;
+      ctx->totals.grad_ms += ms;
+      ctx->totals.grad_flop += p.flop;
+    }
+    ctx->free_events.push_back({p.a, p.b});
+  }
+  ctx->pending.clear();
 }
 
 static int dp_for(int d) { return d <= 2 ? 2 : d <= 4 ? 4 : d <= 8 ? 8 : 16; }
@@ -154,6 +202,7 @@ static ulisse_status prescale(ulisse_ctx* ctx) {
     prescale_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
         ctx->psi_dev, ctx->X, (float*)ctx->xhat, ctx->n, ctx->d, ctx->DP, ctx->params);
   CK(cudaGetLastError());
+  ctx->launches++;
   return ULISSE_OK;
 }
 
@@ -184,8 +233,20 @@ static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, in
       L.partials_bytes = ctx->partials_bytes;
       L.counters = ctx->counters;
       L.counters_len = ctx->counters_len;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      prof_begin(ctx, &ea, &eb);
       cudaError_t e = ctx->f64 ? launch_kmv_f64(L, ctx->stream) : launch_kmv_f32(L, ctx->stream);
-      if (e == cudaSuccess) break;
+      if (ctx->prof) {
+        if (e == cudaSuccess)
+          prof_end(ctx, 0, ea, eb,
+                   (double)ctx->n * ctx->n * (3.0 * ctx->d + 2.0 + 2.0 * L.R));
+        else
+          ctx->free_events.push_back({ea, eb});
+      }
+      if (e == cudaSuccess) {
+        ctx->launches++;
+        break;
+      }
       if (e != cudaErrorMemoryAllocation || attempt == 1)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("K V launch: ") + cudaGetErrorString(e));
       cudaGetLastError();
@@ -214,6 +275,7 @@ static ulisse_status read_status(ulisse_ctx* ctx, int* status) {
   CK(cudaMemcpyAsync(ctx->h_status, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  prof_drain(ctx);
   *status = *ctx->h_status;
   return ULISSE_OK;
 }
@@ -280,18 +342,22 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned lon
   }
   cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
   CK(cudaGetLastError());
+  ctx->launches++;
   for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
     compact_kernel<<<1, 32, 0, ctx->stream>>>(ctx->st, R, ctx->live, ctx->n_live_dev);
     CK(cudaGetLastError());
+    ctx->launches++;
     CK(cudaMemcpyAsync(ctx->h_n_live, ctx->n_live_dev, sizeof(int), cudaMemcpyDeviceToHost,
                        ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    prof_drain(ctx);
     const int nl = *ctx->h_n_live;
     if (nl == 0) break;
     CKS(run_kmv(ctx, ctx->D, ctx->live, nl, ctx->KD, ctx->live, kModeK, -1));
     ctx->mvp_rounds += 1;
     cg_iter_kernel<T><<<nl, kCgNT, 0, ctx->stream>>>(a);
     CK(cudaGetLastError());
+    ctx->launches++;
   }
   return ULISSE_OK;
 }
@@ -354,8 +420,19 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
   for (int attempt = 0; attempt < 2; ++attempt) {
     L.partials = ctx->gpart;
     L.partials_len = ctx->gpart_len;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    prof_begin(ctx, &ea, &eb);
     cudaError_t e = ctx->f64 ? launch_grad_f64(L, ctx->stream) : launch_grad_f32(L, ctx->stream);
-    if (e == cudaSuccess) break;
+    if (ctx->prof) {
+      if (e == cudaSuccess)
+        prof_end(ctx, 1, ea, eb, (double)ctx->n * ctx->n * (5.0 * ctx->d + 4.0 + 2.0 * M));
+      else
+        ctx->free_events.push_back({ea, eb});
+    }
+    if (e == cudaSuccess) {
+      ctx->launches++;
+      break;
+    }
     if (e != cudaErrorMemoryAllocation || attempt == 1)
       return fail(ctx, ULISSE_ERR_CUDA, std::string("gradient launch: ") + cudaGetErrorString(e));
     cudaGetLastError();
@@ -387,6 +464,7 @@ static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step) {
     probes_kernel<float><<<pg, 256, 0, ctx->stream>>>((float*)ctx->B, ctx->ldn, ctx->n, nr,
                                                        ctx->cfg.probe_kind, ctx->cfg.seed, epoch);
   CK(cudaGetLastError());
+  ctx->launches++;
   std::vector<int> n_est(R, 1);
   n_est[0] = 2;
   int tot = 0;
@@ -681,6 +759,7 @@ ulisse_status ulisse_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t,
                                          ctx->d + 2, ctx->cfg.seed, step, nullptr,
                                          ctx->status_dev);
   CK(cudaGetLastError());
+  ctx->launches++;
   int st = 0;
   CKS(read_status(ctx, &st));
   ulisse_status r = status_to_result(ctx, st);
@@ -713,6 +792,7 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
                                            trace_dev ? trace_dev + (long long)k * p : nullptr,
                                            ctx->status_dev);
     CK(cudaGetLastError());
+    ctx->launches++;
   }
   CK(cudaMemcpyAsync(psi_dev, ctx->psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
                      ctx->stream));
@@ -721,10 +801,30 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
   return status_to_result(ctx, st);
 }
 
-ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs) {
+ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,
+                              long long* kernel_launches) {
   if (!ctx) return ULISSE_ERR_ARG;
   if (mvp_rounds) *mvp_rounds = ctx->mvp_rounds;
   if (entry_rhs) *entry_rhs = ctx->entry_rhs;
+  if (kernel_launches) *kernel_launches = ctx->launches;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_profile_enable(ulisse_ctx* ctx, int enable) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_drain(ctx);
+  ctx->prof = enable != 0;
+  ctx->totals = ulisse_profile{};
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_profile_read(ulisse_ctx* ctx, ulisse_profile* out, int reset) {
+  if (!ctx || !out) return ULISSE_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_drain(ctx);
+  *out = ctx->totals;
+  if (reset) ctx->totals = ulisse_profile{};
   return ULISSE_OK;
 }
 
@@ -747,6 +847,11 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->M_dev), reinterpret_cast<void**>(&ctx->prior_dev),
                    reinterpret_cast<void**>(&ctx->status_dev)})
     dev_free(*p);
+  prof_drain(ctx);
+  for (auto& e : ctx->free_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
   if (ctx->h_n_live) cudaFreeHost(ctx->h_n_live);
   if (ctx->h_status) cudaFreeHost(ctx->h_status);
   delete ctx;

@@ -30,7 +30,8 @@ PROBE_RADEMACHER, PROBE_GAUSSIAN = 0, 1
 EXPORTED = [
     "ulisse_config_default", "ulisse_create", "ulisse_create_host", "ulisse_kmv",
     "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
-    "ulisse_counters", "ulisse_last_error", "ulisse_destroy",
+    "ulisse_counters", "ulisse_profile_enable", "ulisse_profile_read", "ulisse_last_error",
+    "ulisse_destroy",
 ]
 
 
@@ -52,6 +53,12 @@ class ulisse_config(ctypes.Structure):
 class ulisse_col_stats(ctypes.Structure):
     _fields_ = [("l", ctypes.c_int), ("iterations", ctypes.c_int), ("outcome", ctypes.c_int),
                 ("J0", ctypes.c_int), ("J1", ctypes.c_int)]
+
+
+class ulisse_profile(ctypes.Structure):
+    _fields_ = [("kmv_launches", ctypes.c_longlong), ("kmv_ms", ctypes.c_double),
+                ("kmv_flop", ctypes.c_double), ("grad_launches", ctypes.c_longlong),
+                ("grad_ms", ctypes.c_double), ("grad_flop", ctypes.c_double)]
 
 
 class UlisseError(RuntimeError):
@@ -87,7 +94,9 @@ def load():
     lib.ulisse_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
     lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
-    lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D)]
+    lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
+    lib.ulisse_profile_enable.argtypes = [P, I]
+    lib.ulisse_profile_read.argtypes = [P, ctypes.POINTER(ulisse_profile), I]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -246,10 +255,21 @@ class Context:
         return psi_dev
 
     def counters(self):
+        """(K V rounds, generated entries x right-hand sides, kernel launches) so far."""
         a = ctypes.c_longlong()
         b = ctypes.c_double()
-        self._lib.ulisse_counters(self._h, ctypes.byref(a), ctypes.byref(b))
-        return a.value, b.value
+        c = ctypes.c_longlong()
+        self._lib.ulisse_counters(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+        return a.value, b.value, c.value
+
+    def profile_enable(self, enable=True):
+        self._check(self._lib.ulisse_profile_enable(self._h, 1 if enable else 0))
+
+    def profile_read(self, reset=False):
+        """Event-timed totals of the K V and gradient kernels since enabling (a dict)."""
+        pr = ulisse_profile()
+        self._check(self._lib.ulisse_profile_read(self._h, ctypes.byref(pr), 1 if reset else 0))
+        return {k: getattr(pr, k) for k, _ in ulisse_profile._fields_}
 
 
 # Same names as the C ABI, for callers that prefer functions over the class.
@@ -287,6 +307,14 @@ def ulisse_sgld_chain(ctx: Context, psi_dev, eps_dev, step0=0, M=None, prior_gra
 
 def ulisse_counters(ctx: Context):
     return ctx.counters()
+
+
+def ulisse_profile_enable(ctx: Context, enable=True):
+    ctx.profile_enable(enable)
+
+
+def ulisse_profile_read(ctx: Context, reset=False):
+    return ctx.profile_read(reset)
 
 
 def ulisse_destroy(ctx: Context):

@@ -182,6 +182,10 @@ def test_kmv_rows_vs_dense(orc):
         assert np.max(np.abs(orc.kmv_rows(X, psi, V, rows, which) - (A @ V)[rows])) < 1e-12
         absu = orc.kmv_rows(X, psi, V, rows, which, absolute=True)
         assert np.max(np.abs(absu - (np.abs(A) @ np.abs(V))[rows])) < 1e-12
+    allr = orc.dkmv_all_rows(X, psi, V, rows)
+    for q in range(d + 2):
+        A = orc.cov_matrix(X, psi, q)
+        assert np.max(np.abs(allr[q] - (A @ V)[rows])) < 1e-12
 
 
 # ----------------------------------------------------------------------------------------
