@@ -116,6 +116,37 @@ ulisse_status ulisse_kmv(ulisse_ctx *ctx, const double *psi, int which, const fl
 ulisse_status ulisse_kmv_f64(ulisse_ctx *ctx, const double *psi, int which, const double *V,
                              int R, double *U);
 
+/*
+ * K V for callers that cannot allocate device memory.  The paper has no counterpart: this
+ * is a deployment variant of ulisse_kmv.  Some callers must not call cudaMalloc -- for
+ * example code running inside a host application that owns the device memory budget and
+ * forbids allocations by the libraries it loads, or a latency-critical loop where an
+ * allocation (with the device synchronisation it may imply) is not acceptable.  They can
+ * still compute U = A V, A = K(psi) (which == -1) or dK/dpsi_which, with this call: it
+ * creates no context and calls no cudaMalloc, cudaFree or allocating library routine.
+ *   X      device, n x d float, row-major (as for ulisse_create); read only.
+ *   n, d   1 <= d <= 16; see the size limit below.
+ *   psi    host, d + 2 doubles.   which: -1 or 0 <= which < d + 2.
+ *   V      device, n x R column-major (leading dimension n), 1 <= R <= 32.
+ *   U      device, n x R column-major output; must not overlap V.
+ *   stream cudaStream_t (as void*) the work is ordered on; the call is asynchronous.
+ * Scratch: one static device array of 64 MiB (reserved on every GPU that loads the
+ * library, until the process exits) holds the prescaled inputs, a zero-padded copy of V,
+ * the split partial sums and the counters.  Size limit: (n rounded up to a multiple of
+ * 64) x (d rounded up to 2, 4, 8 or 16, plus R) floats must fit in 16 MiB (for d = 8 and
+ * R = 17, n <= 167,000); larger requests return ULISSE_ERR_ARG without touching the GPU.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the array: each call clears the parts that must start at zero, but two
+ * calls whose GPU work overlaps (different streams, or different host threads) race on it
+ * and may return wrong results.  Serialise them.
+ * Errors: ULISSE_ERR_ARG (null pointer, sizes out of range or too large, non-finite psi),
+ * ULISSE_ERR_CUDA (no device, or a launch or copy failed).  Device-side timeouts of the
+ * bounded waits are not reported by this call.
+ */
+ulisse_status ulisse_kmv_noalloc(const float *X, long long n, int d, const double *psi,
+                                 int which, const float *V, int R, float *U, void *stream);
+
 /* Per-column outcome of a solve, written to host memory when requested. */
 typedef struct {
     int l;          /* early-stop iteration (first i >= 1 with ||e_i|| < q sqrt(n)); 0 = never */

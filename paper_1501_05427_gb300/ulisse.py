@@ -31,7 +31,7 @@ EXPORTED = [
     "ulisse_config_default", "ulisse_create", "ulisse_create_host", "ulisse_kmv",
     "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
     "ulisse_counters", "ulisse_profile_enable", "ulisse_profile_read", "ulisse_last_error",
-    "ulisse_destroy",
+    "ulisse_destroy", "ulisse_kmv_noalloc",
 ]
 
 
@@ -97,6 +97,7 @@ def load():
     lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
     lib.ulisse_profile_enable.argtypes = [P, I]
     lib.ulisse_profile_read.argtypes = [P, ctypes.POINTER(ulisse_profile), I]
+    lib.ulisse_kmv_noalloc.argtypes = [P, LL, I, P, I, P, I, P, P]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -315,6 +316,28 @@ def ulisse_profile_enable(ctx: Context, enable=True):
 
 def ulisse_profile_read(ctx: Context, reset=False):
     return ctx.profile_read(reset)
+
+
+def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
+    """U = K V (or dK/dpsi_which V) through the allocation-free entry point: X (n, d) and
+    V (n, R <= 32) CUDA float tensors; the library allocates nothing for this call."""
+    import torch
+    lib = load()
+    X = X.contiguous().float()
+    n, d = X.shape
+    Vc = _colmajor(V.float())
+    R = Vc.shape[1]
+    if out is None:
+        out = torch.empty((R, n), dtype=torch.float32, device=V.device).t()
+    psi = _f64_host(psi, d + 2)
+    stream = stream if stream is not None else torch.cuda.current_stream(V.device)
+    st = lib.ulisse_kmv_noalloc(ctypes.c_void_p(X.data_ptr()), n, d, _hptr(psi), which,
+                                ctypes.c_void_p(Vc.data_ptr()), R,
+                                ctypes.c_void_p(out.data_ptr()),
+                                ctypes.c_void_p(stream.cuda_stream))
+    if st != ULISSE_OK:
+        raise UlisseError(st, "ulisse_kmv_noalloc rejected the call")
+    return out[:, 0] if V.dim() == 1 else out
 
 
 def ulisse_destroy(ctx: Context):
