@@ -76,10 +76,13 @@ typedef struct {
     double eps;              /* CG convergence threshold on ||e|| (Algorithm 1; paper: 1e-8) */
     int max_iter;            /* cap on CG iterations per solve (>= 1) */
     unsigned long long seed; /* key of the counter-based generator */
+    int kmv_rows_per_thread; /* K V tile shape: output rows per thread, 2 or 4; 0 = the
+                                tuned default.  Changes the summation order of the split
+                                j range, hence the last bits of the results. */
 } ulisse_config;
 
 /* Fill *cfg with the paper's settings: FP32, 4 Rademacher probes redrawn every step,
- * q = 1, beta = 1, eps = 1e-8, max_iter = 1000, seed 0. */
+ * q = 1, beta = 1, eps = 1e-8, max_iter = 1000, seed 0, tuned K V tile shape. */
 void ulisse_config_default(ulisse_config *cfg);
 
 /*

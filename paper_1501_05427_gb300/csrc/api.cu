@@ -31,6 +31,9 @@ struct ulisse_ctx {
   int cap_est = 0;            // column capacity of SE
   void *B = nullptr, *S = nullptr, *E = nullptr, *D = nullptr, *KD = nullptr, *SE = nullptr;
   ColState* st = nullptr;
+  ColState* st_next = nullptr;
+  double* part1 = nullptr;     // CG partial dot products, cap x kMaxCgChunks each
+  double* part2 = nullptr;
   int* live = nullptr;
   int* n_live_dev = nullptr;
   int* iota = nullptr;        // 0, 1, 2, ... (cap entries)
@@ -69,6 +72,7 @@ struct ulisse_ctx {
 };
 
 static thread_local std::string g_create_error;
+static constexpr int kMaxCgChunks = 64;
 
 #define CK(call)                                                                     \
   do {                                                                               \
@@ -158,6 +162,9 @@ static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
   CK(cudaStreamSynchronize(ctx->stream));
   for (void** p : {&ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD, &ctx->SE}) dev_free(*p);
   dev_free(reinterpret_cast<void*&>(ctx->st));
+  dev_free(reinterpret_cast<void*&>(ctx->st_next));
+  dev_free(reinterpret_cast<void*&>(ctx->part1));
+  dev_free(reinterpret_cast<void*&>(ctx->part2));
   dev_free(reinterpret_cast<void*&>(ctx->live));
   dev_free(reinterpret_cast<void*&>(ctx->iota));
   const size_t col = (size_t)ctx->ldn * ctx->esz;
@@ -165,6 +172,9 @@ static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
     CKS(dev_alloc(ctx, p, col * cap));
   CKS(dev_alloc(ctx, &ctx->SE, col * cap_est));
   CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->st), sizeof(ColState) * cap));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->st_next), sizeof(ColState) * cap));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->part1), sizeof(double) * cap * kMaxCgChunks));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->part2), sizeof(double) * cap * kMaxCgChunks));
   CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->live), sizeof(int) * cap));
   const int ni = std::max(cap, cap_est);
   CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->iota), sizeof(int) * ni));
@@ -226,6 +236,7 @@ static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, in
     L.params = ctx->params;
     L.mode = mode;
     L.which = which;
+    L.tm = ctx->cfg.kmv_rows_per_thread;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -301,6 +312,11 @@ static CgArgs<T> cg_args(ulisse_ctx* ctx, int has_s0, unsigned long long step) {
   a.n = ctx->n;
   a.ld = ctx->ldn;
   a.st = ctx->st;
+  a.st_next = ctx->st_next;
+  a.part1 = ctx->part1;
+  a.part2 = ctx->part2;
+  a.nchunk = 1;
+  a.chunk = ctx->n;
   a.live = ctx->live;
   a.alpha_thr = ctx->cfg.q * std::sqrt((double)ctx->n);
   a.eps = ctx->cfg.eps;
@@ -343,8 +359,10 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned lon
   cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
   CK(cudaGetLastError());
   ctx->launches++;
+  int n_prev = 0;
   for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
-    compact_kernel<<<1, 32, 0, ctx->stream>>>(ctx->st, R, ctx->live, ctx->n_live_dev);
+    compact_kernel<<<1, 32, 0, ctx->stream>>>(ctx->st, ctx->st_next, R, n_prev, ctx->live,
+                                              ctx->n_live_dev);
     CK(cudaGetLastError());
     ctx->launches++;
     CK(cudaMemcpyAsync(ctx->h_n_live, ctx->n_live_dev, sizeof(int), cudaMemcpyDeviceToHost,
@@ -355,9 +373,20 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned lon
     if (nl == 0) break;
     CKS(run_kmv(ctx, ctx->D, ctx->live, nl, ctx->KD, ctx->live, kModeK, -1));
     ctx->mvp_rounds += 1;
-    cg_iter_kernel<T><<<nl, kCgNT, 0, ctx->stream>>>(a);
+    // Spread the live columns over about two waves of CTAs (at least 2048 rows each).
+    const long long target = std::max(1, (2 * ctx->num_sms + nl - 1) / nl);
+    long long ch = std::max<long long>((ctx->n + target - 1) / target, 2048);
+    ch = std::max<long long>(ch, (ctx->n + kMaxCgChunks - 1) / kMaxCgChunks);
+    ch = (ch + 255) / 256 * 256;
+    a.chunk = ch;
+    a.nchunk = (int)((ctx->n + ch - 1) / ch);
+    const dim3 grid(a.nchunk, nl);
+    cg_dot_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+    cg_update_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+    cg_finish_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
     CK(cudaGetLastError());
-    ctx->launches++;
+    ctx->launches += 3;
+    n_prev = nl;
   }
   return ULISSE_OK;
 }
@@ -486,6 +515,8 @@ static ulisse_status check_cfg(const ulisse_config* c) {
   if (!(c->q >= 0.0) || !(c->beta > 0.0) || !(c->eps >= 0.0)) return ULISSE_ERR_ARG;
   if (!std::isfinite(c->q) || !std::isfinite(c->beta) || !std::isfinite(c->eps))
     return ULISSE_ERR_ARG;
+  if (c->kmv_rows_per_thread != 0 && c->kmv_rows_per_thread != 2 && c->kmv_rows_per_thread != 4)
+    return ULISSE_ERR_ARG;
   return ULISSE_OK;
 }
 
@@ -589,6 +620,7 @@ void ulisse_config_default(ulisse_config* cfg) {
   cfg->eps = 1e-8;
   cfg->max_iter = 1000;
   cfg->seed = 0;
+  cfg->kmv_rows_per_thread = 0;
 }
 
 ulisse_status ulisse_create(ulisse_ctx** out, const float* X, const float* y, long long n, int d,
@@ -835,6 +867,9 @@ const char* ulisse_last_error(const ulisse_ctx* ctx) {
 void ulisse_destroy(ulisse_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (void** p : {reinterpret_cast<void**>(&ctx->st_next), reinterpret_cast<void**>(&ctx->part1),
+                   reinterpret_cast<void**>(&ctx->part2)})
+    dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,
                    reinterpret_cast<void**>(&ctx->params), reinterpret_cast<void**>(&ctx->psi_dev),
                    &ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD, &ctx->SE,

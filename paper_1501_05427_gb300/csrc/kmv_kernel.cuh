@@ -68,7 +68,9 @@ __device__ __forceinline__ T kernel_from_dist(T dist, float c0, float c1, double
   }
 }
 
-template <typename T, int DP, int R, int TM, int NT>
+// MODE (compile time): kModeK (K), kModeDLen (dK/dlog l_which), kModeDSig (dK/dlog sigma^2),
+// 3 (dK/dlog lambda = lambda I: no tiles, only the diagonal term).
+template <typename T, int DP, int R, int TM, int NT, int MODE>
 __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   constexpr int BM = NT * TM;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   const long long row0 = (long long)rb * BM;
   const int tile_begin = sp * a.tiles_per_split;
   const int tile_end = min(tile_begin + a.tiles_per_split, a.ntiles);
-  const int nt_local = (a.mode == 3) ? 0 : max(0, tile_end - tile_begin);
+  const int nt_local = (MODE == 3) ? 0 : max(0, tile_end - tile_begin);
   const int Ra = a.R;
 
   const float c0 = a.params->c0f, c1 = a.params->c1f;
@@ -130,7 +132,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
 #pragma unroll
       for (int k = 0; k < DP; ++k) xi[t][k] = T(0);
     }
-    xiw[t] = (a.mode == kModeDLen && i < a.n) ? a.xhat[i * DP + a.which] : T(0);
+    xiw[t] = (MODE == kModeDLen && i < a.n) ? a.xhat[i * DP + a.which] : T(0);
   }
 
   T acc[TM][R];
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
               dist = fma(df, df, dist);
             }
             T kv = kernel_from_dist<T>(dist, c0, c1, sigma2);
-            if (a.mode == kModeDLen) {
+            if constexpr (MODE == kModeDLen) {
               const T dw = xiw[t] - tX[(jq + q) * DP + a.which];
               kv *= dw * dw;
             }
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   }
 
   // Diagonal term lambda V (K) or the whole product (dK/dlog lambda = lambda I).
-  const bool add_diag = (a.mode == kModeK || a.mode == 3);
+  constexpr bool add_diag = (MODE == kModeK || MODE == 3);
   if (a.nsplit == 1) {
 #pragma unroll
     for (int t = 0; t < TM; ++t) {
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
       for (int r = 0; r < R; ++r) {
         if (r >= Ra) break;
         T u = acc[t][r];
-        if (add_diag) u = fma(lam, a.V[(long long)s_vcol[r] * a.ldv + i], u);
+        if constexpr (add_diag) u = fma(lam, a.V[(long long)s_vcol[r] * a.ldv + i], u);
         a.U[(long long)a.umap[r] * a.ldu + i] = u;
       }
     }
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
       T u = T(0);
       for (int s2 = 0; s2 < a.nsplit; ++s2)
         u += __ldcg(base + ((long long)s2 * R + r) * BM + t * NT + tid);
-      if (add_diag) u = fma(lam, a.V[(long long)s_vcol[r] * a.ldv + i], u);
+      if constexpr (add_diag) u = fma(lam, a.V[(long long)s_vcol[r] * a.ldv + i], u);
       a.U[(long long)a.umap[r] * a.ldu + i] = u;
     }
   }

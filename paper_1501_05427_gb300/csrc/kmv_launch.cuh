@@ -12,7 +12,7 @@ namespace ulisse {
 
 constexpr int kKmvNT = 128;
 
-template <typename T, int DP, int R, int TM>
+template <typename T, int DP, int R, int TM, int MODE>
 struct KmvInst {
   static constexpr int BM = kKmvNT * TM;
   static size_t smem_bytes() {
@@ -22,7 +22,7 @@ struct KmvInst {
     static int occ = -1;
     static std::once_flag once;
     std::call_once(once, [] {
-      auto fn = kmv_kernel<T, DP, R, TM, kKmvNT>;
+      auto fn = kmv_kernel<T, DP, R, TM, kKmvNT, MODE>;
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes());
       int o = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kKmvNT, smem_bytes()) !=
@@ -37,7 +37,7 @@ struct KmvInst {
   }
   static cudaError_t launch(KmvLaunch& L, cudaStream_t s) {
     KmvPlan p = plan(L);
-    if (L.mode == 3) {  // dK/dlog lambda = lambda I: no tiles, one CTA per row block
+    if (MODE == 3) {  // dK/dlog lambda = lambda I: no tiles, one CTA per row block
       p.nsplit = 1;
       p.tiles_per_split = 0;
       p.partial_bytes = 0;
@@ -69,7 +69,7 @@ struct KmvInst {
     a.counters = L.counters;
     a.status = L.status;
     (void)occupancy();
-    kmv_kernel<T, DP, R, TM, kKmvNT><<<p.n_rb * p.nsplit, kKmvNT, smem_bytes(), s>>>(a);
+    kmv_kernel<T, DP, R, TM, kKmvNT, MODE><<<p.n_rb * p.nsplit, kKmvNT, smem_bytes(), s>>>(a);
     return cudaGetLastError();
   }
 };
@@ -78,11 +78,26 @@ struct KmvInst {
 template <int... Rs>
 struct RList {};
 
-template <typename T, int DP, int TM, int R0, int... Rs>
+template <typename T, int DP, int TM, int MODE, int R0, int... Rs>
 cudaError_t dispatch_r(KmvLaunch& L, cudaStream_t s, RList<R0, Rs...>) {
-  if (L.R <= R0 || sizeof...(Rs) == 0) return KmvInst<T, DP, R0, TM>::launch(L, s);
-  if constexpr (sizeof...(Rs) > 0) return dispatch_r<T, DP, TM>(L, s, RList<Rs...>{});
+  if (L.R <= R0 || sizeof...(Rs) == 0) return KmvInst<T, DP, R0, TM, MODE>::launch(L, s);
+  if constexpr (sizeof...(Rs) > 0) return dispatch_r<T, DP, TM, MODE>(L, s, RList<Rs...>{});
   return cudaErrorInvalidValue;
+}
+
+// Mode and rows-per-thread dispatch for one DP.  K uses the tuned rows per thread
+// (L.tm: 2 or 4); the derivative products use 2 rows per thread and a shorter R list.
+template <typename T, int DP, int TMK, int TMK2, typename RK, typename RD>
+cudaError_t dispatch_mode(KmvLaunch& L, cudaStream_t s) {
+  switch (L.mode) {
+    case kModeK:
+      if (L.tm == TMK2) return dispatch_r<T, DP, TMK2, kModeK>(L, s, RK{});
+      return dispatch_r<T, DP, TMK, kModeK>(L, s, RK{});
+    case kModeDLen: return dispatch_r<T, DP, TMK, kModeDLen>(L, s, RD{});
+    case kModeDSig: return dispatch_r<T, DP, TMK, kModeDSig>(L, s, RD{});
+    case 3: return dispatch_r<T, DP, TMK, 3>(L, s, RD{});
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace ulisse

@@ -40,7 +40,12 @@ struct CgArgs {
   T* SE;         // ULISSE estimates
   long long n, ld;
   ColState* st;
+  ColState* st_next;     // state written by an iteration, committed by compact_kernel
   const int* live;
+  double* part1;         // per (column, chunk) partial d^T K d
+  double* part2;         // per (column, chunk) partial e^T e
+  int nchunk;            // CTAs per column
+  long long chunk;       // rows per CTA
   double alpha_thr, eps, beta;
   int max_iter;
   int has_s0;
@@ -109,54 +114,67 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   }
 }
 
-// One CG iteration (Algorithm 1) on every live column, with the ULISSE bookkeeping:
-// the increment delta_{m+1} = alpha_m d_m is added with weight prod_{r<=j} w_r to every
-// estimator whose J >= j (j = m+1-l) once the early stop at l has been reached; at l the
-// estimators start from s_l.  One CTA per live column.
+// One CG iteration (Algorithm 1) on every live column, with the ULISSE bookkeeping, in
+// three launches over a (chunk, live column) grid so that every column is spread over
+// several CTAs:
+//   cg_dot_kernel     partial d^T K d per chunk
+//   cg_update_kernel  alpha = e^T e / d^T K d (partials summed in chunk order), s += alpha d,
+//                     e -= alpha K d, the ULISSE tail term, partial e'^T e' per chunk
+//   cg_finish_kernel  e'^T e' (chunk order), the early-stop / convergence / max_iter
+//                     decisions (every CTA of a column reaches the same ones), the copy of
+//                     s_l into the estimators at the early stop, d = e' + beta d, and the
+//                     new column state (into st_next; compact_kernel commits it).
+// The increment delta_{m+1} = alpha_m d_m is added with weight prod_{r<=j} w_r to every
+// estimator whose J >= j (j = m+1-l) once the early stop at l has been reached.
+constexpr int kCgChunkNT = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(kCgNT) cg_iter_kernel(const CgArgs<T> a) {
-  __shared__ double red[kCgNT / 32];
-  const int c = a.live[blockIdx.x];
-  ColState& st = a.st[c];
+__device__ inline void chunk_range(const CgArgs<T>& a, long long* i0, long long* i1) {
+  *i0 = (long long)blockIdx.x * a.chunk;
+  *i1 = min(a.n, *i0 + a.chunk);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_dot_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgChunkNT / 32];
+  const int c = a.live[blockIdx.y];
+  const T* d = a.D + c * a.ld;
+  const T* kd = a.KD + c * a.ld;
+  long long i0, i1;
+  chunk_range(a, &i0, &i1);
+  double p = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) p += (double)d[i] * (double)kd[i];
+  p = block_sum<kCgChunkNT>(p, red);
+  if (threadIdx.x == 0) a.part1[(long long)c * a.nchunk + blockIdx.x] = p;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_update_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgChunkNT / 32];
+  const int c = a.live[blockIdx.y];
+  const ColState& st = a.st[c];
+  double dKd = 0.0;
+  for (int k = 0; k < a.nchunk; ++k) dKd += a.part1[(long long)c * a.nchunk + k];
+  if (!(dKd > 0.0) || !isfinite(dKd)) return;  // breakdown: handled in cg_finish_kernel
   T* s = a.S + c * a.ld;
   T* e = a.E + c * a.ld;
-  T* d = a.D + c * a.ld;
+  const T* d = a.D + c * a.ld;
   const T* kd = a.KD + c * a.ld;
-  const double ee = st.ee;
-  const int phase = st.phase, l = st.l, m = st.m, n_est = st.n_est, outcome0 = st.outcome;
-  const int J0 = st.J[0], J1 = st.J[1];
-  T* se0 = a.SE + (long long)st.est_off * a.ld;
-  T* se1 = se0 + a.ld;
-
-  double p = 0.0;
-  for (long long i = threadIdx.x; i < a.n; i += kCgNT) p += (double)d[i] * (double)kd[i];
-  const double dKd = block_sum<kCgNT>(p, red);
-  if (!(dKd > 0.0) || !isfinite(dKd)) {
-    // Breakdown: K is not positive definite along d, or a value is not finite.
-    if (phase == kPre)
-      for (int t = 0; t < n_est; ++t) {
-        T* se = se0 + t * a.ld;
-        for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
-      }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      st.outcome = 3;
-      st.phase = kDone;
-      atomicOr(a.status, kStatusBreakdown);
-    }
-    return;
-  }
-  const double al = ee / dKd;
+  const double al = st.ee / dKd;
   const T alT = (T)al;
   T w0 = T(0), w1 = T(0);
-  if (phase == kTail) {
-    const int j = m + 1 - l;
+  if (st.phase == kTail) {
+    const int j = st.m + 1 - st.l;
     const double Wa = weight_product(j, a.beta) * al;
-    if (J0 >= j) w0 = (T)Wa;
-    if (n_est > 1 && J1 >= j) w1 = (T)Wa;
+    if (st.J[0] >= j) w0 = (T)Wa;
+    if (st.n_est > 1 && st.J[1] >= j) w1 = (T)Wa;
   }
+  T* se0 = a.SE + (long long)st.est_off * a.ld;
+  T* se1 = se0 + a.ld;
+  long long i0, i1;
+  chunk_range(a, &i0, &i1);
   double p2 = 0.0;
-  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
+  for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) {
     const T di = d[i];
     s[i] = fma(alT, di, s[i]);
     const T ei = fma(-alT, kd[i], e[i]);
@@ -165,10 +183,43 @@ __global__ void __launch_bounds__(kCgNT) cg_iter_kernel(const CgArgs<T> a) {
     if (w0 != T(0)) se0[i] = fma(w0, di, se0[i]);
     if (w1 != T(0)) se1[i] = fma(w1, di, se1[i]);
   }
-  const double ee1 = block_sum<kCgNT>(p2, red);
+  p2 = block_sum<kCgChunkNT>(p2, red);
+  if (threadIdx.x == 0) a.part2[(long long)c * a.nchunk + blockIdx.x] = p2;
+}
 
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a) {
+  const int c = a.live[blockIdx.y];
+  const ColState& st = a.st[c];
+  const int phase = st.phase, l = st.l, m = st.m, n_est = st.n_est;
+  const int J0 = st.J[0], J1 = st.J[1];
+  T* s = a.S + c * a.ld;
+  T* e = a.E + c * a.ld;
+  T* d = a.D + c * a.ld;
+  T* se0 = a.SE + (long long)st.est_off * a.ld;
+  long long i0, i1;
+  chunk_range(a, &i0, &i1);
+  double dKd = 0.0, ee1 = 0.0;
+  for (int k = 0; k < a.nchunk; ++k) {
+    dKd += a.part1[(long long)c * a.nchunk + k];
+    ee1 += a.part2[(long long)c * a.nchunk + k];
+  }
+  ColState nx = st;
+  if (!(dKd > 0.0) || !isfinite(dKd)) {
+    // Breakdown: K is not positive definite along d, or a value is not finite.
+    if (phase == kPre)
+      for (int t = 0; t < n_est; ++t)
+        for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) se0[t * a.ld + i] = s[i];
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      nx.outcome = 3;
+      nx.phase = kDone;
+      a.st_next[c] = nx;
+      atomicOr(a.status, kStatusBreakdown);
+    }
+    return;
+  }
   const int m1 = m + 1;
-  int ph = phase, l1 = l, outcome = outcome0;
+  int ph = phase, l1 = l, outcome = st.outcome;
   bool copy_s = false, done = false;
   const int jmax = (n_est > 1 && J1 > J0) ? J1 : J0;
   if (ph == kPre && sqrt(ee1) < a.alpha_thr) {
@@ -188,29 +239,30 @@ __global__ void __launch_bounds__(kCgNT) cg_iter_kernel(const CgArgs<T> a) {
     done = true;
   }
   if (copy_s)
-    for (int t = 0; t < n_est; ++t) {
-      T* se = se0 + t * a.ld;
-      for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
-    }
+    for (int t = 0; t < n_est; ++t)
+      for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) se0[t * a.ld + i] = s[i];
   if (!done) {
-    const T btT = (T)(ee1 / ee);
-    for (long long i = threadIdx.x; i < a.n; i += kCgNT) d[i] = fma(btT, d[i], e[i]);
+    const T btT = (T)(ee1 / st.ee);
+    for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) d[i] = fma(btT, d[i], e[i]);
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    st.ee = ee1;
-    st.m = m1;
-    st.l = l1;
-    st.outcome = outcome;
-    st.phase = done ? kDone : ph;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    nx.ee = ee1;
+    nx.m = m1;
+    nx.l = l1;
+    nx.outcome = outcome;
+    nx.phase = done ? kDone : ph;
+    a.st_next[c] = nx;
     if (outcome == 4) atomicOr(a.status, kStatusMaxIter);
   }
 }
 
-// Live list of the columns still iterating, in column order; count to *n_live.
-__global__ void compact_kernel(const ColState* __restrict__ st, int R, int* __restrict__ live,
+// Commit the state of the columns that just iterated (the first n_prev entries of the
+// live list), then rebuild the live list in column order; count to *n_live.
+__global__ void compact_kernel(ColState* __restrict__ st, const ColState* __restrict__ st_next,
+                               int R, int n_prev, int* __restrict__ live,
                                int* __restrict__ n_live) {
   if (threadIdx.x != 0) return;
+  for (int k = 0; k < n_prev; ++k) st[live[k]] = st_next[live[k]];
   int k = 0;
   for (int c = 0; c < R; ++c)
     if (st[c].phase != kDone) live[k++] = c;

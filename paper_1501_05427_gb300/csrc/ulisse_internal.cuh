@@ -193,6 +193,7 @@ struct KmvLaunch {
   const DevParams* params;
   int mode;              // KmvMode
   int which;             // dimension for kModeDLen
+  int tm;                // rows per thread for K (0 = default)
   void* partials;        // split-j scratch
   size_t partials_bytes;
   int* counters;         // one per row block, zero between launches
@@ -228,6 +229,10 @@ struct GradLaunch {
 
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_kmv_f32(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_f32_dp2(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_f32_dp4(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_f32_dp8(KmvLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_f32_dp16(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_f64(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f32(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f64(GradLaunch& L, cudaStream_t s);

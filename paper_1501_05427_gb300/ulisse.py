@@ -47,6 +47,7 @@ class ulisse_config(ctypes.Structure):
         ("eps", ctypes.c_double),
         ("max_iter", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
+        ("kmv_rows_per_thread", ctypes.c_int),
     ]
 
 
