@@ -54,6 +54,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target host time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--path", choices=["fp32", "mixed"], default="fp32",
+                    help="K V path: FP32 SIMT or tensor-core mixed precision")
     return ap.parse_args()
 
 
@@ -258,8 +260,10 @@ def run_ours(args):
     prob = w.census_like()
     n, d = prob.n, prob.d
     p = d + 2
+    prec = u.PREC_MIXED if args.path == "mixed" else u.PREC_FP32
     cfg = u.ulisse_config_default(n_probes=N_PROBES, probe_kind=u.PROBE_RADEMACHER, q=1.0,
-                                  beta=1.0, eps=1e-8, max_iter=1000, seed=20150123 + rank)
+                                  beta=1.0, eps=1e-8, max_iter=1000, seed=20150123 + rank,
+                                  precision=prec)
     X = torch.from_numpy(prob.X).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
     stream = torch.cuda.current_stream(dev)
@@ -336,7 +340,8 @@ def run_ours(args):
         traffic = float(tf["dram_bytes_per_launch"])
     roofline = {
         "bound": "alu",
-        "kernel": "kmv_kernel (tile-generating K V, FP32 SIMT)",
+        "kernel": ("kmv_tc_kernel (tile-generating K V, tcgen05)" if args.path == "mixed"
+                   else "kmv_kernel (tile-generating K V, FP32 SIMT)"),
         "achieved": kmv_tflops,
         "peak": FP32_FMA_PEAK_TFLOPS,
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz max SM clock",
@@ -355,7 +360,9 @@ def run_ours(args):
         "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "d": d, "n_probes": N_PROBES, "q": 1.0,
-                   "beta": 1.0, "eps_t": EPS_T, "path": "fp32 SIMT K V",
+                   "beta": 1.0, "eps_t": EPS_T,
+                   "path": ("tcgen05 mixed K V (3xTF32 cross term, 3xBF16 contraction)"
+                            if args.path == "mixed" else "fp32 SIMT K V"),
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "kv_throughput": {"value": (mvp_erhs * K) / (prof["kmv_ms"] / 1e3)

@@ -19,7 +19,11 @@ struct ulisse_ctx {
   int d = 0, DP = 0;
   ulisse_config cfg{};
   bool f64 = false;
+  bool mixed = false;         // tensor-core K V (tcgen05), FP32 vectors
   size_t esz = 4;
+  long long ld128 = 0;        // rows of the tensor-core operand images (multiple of 128)
+  float* bneg = nullptr;      // -log2(e)/2 |x^|^2 per input (tensor-core path)
+  void *Vt_hi = nullptr, *Vt_lo = nullptr;
 
   float* X = nullptr;         // raw inputs, n x d row-major
   void* y = nullptr;          // labels, ldn (element type T)
@@ -213,12 +217,79 @@ static ulisse_status prescale(ulisse_ctx* ctx) {
         ctx->psi_dev, ctx->X, (float*)ctx->xhat, ctx->n, ctx->d, ctx->DP, ctx->params);
   CK(cudaGetLastError());
   ctx->launches++;
+  if (ctx->mixed) {
+    CK(launch_prescale_tc((const float*)ctx->xhat, ctx->DP, ctx->d, ctx->n, ctx->ld128,
+                          ctx->bneg, ctx->num_sms, ctx->stream));
+    ctx->launches++;
+  }
   return ULISSE_OK;
 }
 
 // U[:, umap[r]] = A V[:, vmap[r]] for r < R (chunks of kMaxRChunk columns per launch).
+static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap, int R, void* U,
+                                const int* umap) {
+  for (int c0 = 0; c0 < R; c0 += 64) {
+    TcLaunch L{};
+    L.xhat = (const float*)ctx->xhat;
+    L.bneg = ctx->bneg;
+    L.V_hi = ctx->Vt_hi;
+    L.V_lo = ctx->Vt_lo;
+    L.V = V;
+    L.ldv = ctx->ldn;
+    L.vmap = vmap + c0;
+    L.R = std::min(64, R - c0);
+    L.U = U;
+    L.ldu = ctx->ldn;
+    L.umap = umap + c0;
+    L.n = ctx->n;
+    L.DP = ctx->DP;
+    L.params = ctx->params;
+    L.status = ctx->status_dev;
+    L.num_sms = ctx->num_sms;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      L.partials = ctx->partials;
+      L.partials_bytes = ctx->partials_bytes;
+      L.counters = ctx->counters;
+      L.counters_len = ctx->counters_len;
+      cudaEvent_t ea = nullptr, eb = nullptr;
+      prof_begin(ctx, &ea, &eb);
+      cudaError_t e = launch_kmv_tc(L, ctx->stream);
+      if (ctx->prof) {
+        if (e == cudaSuccess)
+          prof_end(ctx, 0, ea, eb, (double)ctx->n * ctx->n * (3.0 * ctx->d + 2.0 + 2.0 * L.R));
+        else
+          ctx->free_events.push_back({ea, eb});
+      }
+      if (e == cudaSuccess) {
+        ctx->launches += 2;
+        break;
+      }
+      if (e != cudaErrorMemoryAllocation || attempt == 1)
+        return fail(ctx, ULISSE_ERR_CUDA, std::string("tensor-core K V launch: ") + cudaGetErrorString(e));
+      cudaGetLastError();
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (L.need_partials_bytes > ctx->partials_bytes) {
+        dev_free(ctx->partials);
+        ctx->partials_bytes = 0;
+        CKS(dev_alloc(ctx, &ctx->partials, L.need_partials_bytes));
+        ctx->partials_bytes = L.need_partials_bytes;
+      }
+      if (L.need_counters > ctx->counters_len) {
+        dev_free(reinterpret_cast<void*&>(ctx->counters));
+        ctx->counters_len = 0;
+        CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->counters),
+                      sizeof(int) * L.need_counters));
+        ctx->counters_len = L.need_counters;
+      }
+    }
+    ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
+  }
+  return ULISSE_OK;
+}
+
 static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, int R, void* U,
                              const int* umap, int mode, int which) {
+  if (ctx->mixed && mode == kModeK) return run_kmv_tc(ctx, V, vmap, R, U, umap);
   for (int c0 = 0; c0 < R; c0 += kMaxRChunk) {
     KmvLaunch L{};
     L.xhat = ctx->xhat;
@@ -529,8 +600,6 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
   if (n < 1 || n > 2147483647LL) return fail(nullptr, ULISSE_ERR_ARG, "n out of range");
   if (d < 1 || d > kMaxD) return fail(nullptr, ULISSE_ERR_ARG, "d must be in 1..16");
   if (check_cfg(cfg) != ULISSE_OK) return fail(nullptr, ULISSE_ERR_ARG, "invalid config");
-  if (cfg->precision == ULISSE_PREC_MIXED)
-    return fail(nullptr, ULISSE_ERR_ARG, "mixed precision is not available in this build");
   if (cfg->warm_start_probes)
     return fail(nullptr, ULISSE_ERR_ARG, "warm_start_probes is not available in this build");
   ulisse_ctx* ctx = new ulisse_ctx();
@@ -541,7 +610,9 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
   ctx->DP = dp_for(d);
   ctx->ldn = (n + kBN - 1) / kBN * kBN;
   ctx->f64 = cfg->precision == ULISSE_PREC_FP64;
+  ctx->mixed = cfg->precision == ULISSE_PREC_MIXED;
   ctx->esz = ctx->f64 ? 8 : 4;
+  ctx->ld128 = (n + 127) / 128 * 128;
   auto bail = [&](ulisse_status s) {
     g_create_error = ctx->err;
     ulisse_destroy(ctx);
@@ -569,6 +640,12 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->prior_dev), sizeof(double) * kMaxP)) ||
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))))
     return bail(s);
+  if (ctx->mixed) {
+    if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bneg), sizeof(float) * ctx->ld128)) ||
+        (s = dev_alloc(ctx, &ctx->Vt_hi, 2 * ctx->ld128 * 64)) ||
+        (s = dev_alloc(ctx, &ctx->Vt_lo, 2 * ctx->ld128 * 64)))
+      return bail(s);
+  }
   if (cudaMallocHost(&ctx->h_n_live, sizeof(int)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) {
     ctx->err = "cudaMallocHost failed";
@@ -868,7 +945,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (void** p : {reinterpret_cast<void**>(&ctx->st_next), reinterpret_cast<void**>(&ctx->part1),
-                   reinterpret_cast<void**>(&ctx->part2)})
+                   reinterpret_cast<void**>(&ctx->part2), reinterpret_cast<void**>(&ctx->bneg),
+                   &ctx->Vt_hi, &ctx->Vt_lo})
     dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,
                    reinterpret_cast<void**>(&ctx->params), reinterpret_cast<void**>(&ctx->psi_dev),

@@ -141,6 +141,15 @@ __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Bounded wait for short, latency-critical handoffs (about a second at most).
+__device__ inline bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 25); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > (1 << 16)) __nanosleep(32);
+  }
+  return false;
+}
+
 __device__ inline float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -227,6 +236,32 @@ struct GradLaunch {
   size_t need_partials_len;  // set when partials_len is too small
 };
 
+// Mixed-precision (tcgen05) K V launch: operands prepared by launch_prescale_tc.
+struct TcLaunch {
+  const float* xhat;     // prescaled inputs, ld x DP row-major (the SIMT layout)
+  const float* bneg;     // -c1 |x^|^2 (launch_prescale_tc), ld128
+  void* V_hi;            // BF16 packed operand tiles (written by the launch), ld128 x 64
+  void* V_lo;
+  const void* V;         // FP32 operand columns
+  long long ldv;
+  const int* vmap;
+  int R;                 // right-hand sides (<= 64)
+  void* U;
+  long long ldu;
+  const int* umap;
+  long long n;
+  int DP;
+  const DevParams* params;
+  void* partials;
+  size_t partials_bytes;
+  int* counters;
+  int counters_len;
+  int* status;
+  int num_sms;
+  size_t need_partials_bytes;
+  int need_counters;
+};
+
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_kmv_f32(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_f32_dp2(KmvLaunch& L, cudaStream_t s);
@@ -236,5 +271,8 @@ cudaError_t launch_kmv_f32_dp16(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_f64(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f32(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f64(GradLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_tc(TcLaunch& L, cudaStream_t s);
+cudaError_t launch_prescale_tc(const float* xhat, int DP, int d, long long n, long long ld,
+                               float* bneg, int num_sms, cudaStream_t s);
 
 }  // namespace ulisse

@@ -101,6 +101,50 @@ def test_kmv_full_size_sampled_rows(orc):
     _kv_check(Ug.astype(np.float64), ref, scale, 1e-5)
 
 
+# Mixed precision (tensor cores): the cross term x^_i.x^_j by three TF32 products and the
+# contraction K V by three BF16 products leave every generated entry with a relative error of
+# a few 1e-5 (TF32 split: ~2^-21 of |x^|^2 in the exponent; BF16 split: ~2^-16 per product).
+# Those errors are independent across entries, so each output stays within 1e-4 of its
+# dot-product scale sum_j |K_ij||V_jr|; the norm-wise error is reported by the test.
+MIXED_TOL = 1e-4
+
+
+@pytest.mark.parametrize("n,d,R", [(1, 2, 1), (130, 2, 3), (1000, 8, 17), (2111, 16, 7),
+                                   (3000, 3, 32), (1500, 8, 40), (900, 5, 70)])
+def test_kmv_mixed_tensor_cores(orc, n, d, R):
+    prob = w.random_problem(n, d, seed=700 + n + d) if d != 8 else w.census_like(n=n, seed=700 + n)
+    V = np.random.default_rng(n + R).standard_normal((n, R)).astype(np.float32)
+    Xd = prob.X.astype(np.float64)
+    Vd = V.astype(np.float64)
+    with _ctx(prob, precision=u.PREC_MIXED) as ctx:
+        Ug = ctx.kmv(prob.psi_true, torch.from_numpy(V).cuda()).cpu().numpy().astype(np.float64)
+    A = orc.cov_matrix(Xd, prob.psi_true)
+    ref = A @ Vd
+    scale = np.abs(A) @ np.abs(Vd)
+    comp = np.max(np.abs(Ug - ref) / scale)
+    frob = np.linalg.norm(Ug - ref) / np.linalg.norm(ref)
+    print("mixed K V n=%d d=%d R=%d: max |err|/scale %.2e, Frobenius %.2e" % (n, d, R, comp, frob))
+    assert comp <= MIXED_TOL and frob <= MIXED_TOL
+
+
+def test_kmv_mixed_full_size_sampled_rows(orc):
+    """Near-duplicate workload shape at reduced n (d = 16, 1% jittered copies): the split
+    cross term keeps the near-zero distances accurate."""
+    prob = w.near_duplicates(n=20_000)
+    n = prob.n
+    rng = np.random.default_rng(5)
+    V = rng.choice([-1.0, 1.0], (n, 64)).astype(np.float32)
+    rows = np.sort(rng.choice(n, 32, replace=False))
+    with _ctx(prob, precision=u.PREC_MIXED) as ctx:
+        Ug = ctx.kmv(prob.psi_true, torch.from_numpy(V).cuda()).cpu().numpy()[rows]
+    Xd, Vd = prob.X.astype(np.float64), V.astype(np.float64)
+    ref = orc.kmv_rows(Xd, prob.psi_true, Vd, rows)
+    scale = orc.kmv_rows(Xd, prob.psi_true, Vd, rows, absolute=True)
+    comp = np.max(np.abs(Ug - ref) / scale)
+    print("mixed K V near-duplicates n=%d: max |err|/scale %.2e" % (n, comp))
+    assert comp <= MIXED_TOL
+
+
 def test_kmv_symmetry_and_linearity():
     """Properties that hold at any size: e_i^T K e_j = e_j^T K e_i; K (aV) = a K V."""
     prob = w.random_problem(5000, 4, seed=9)
