@@ -166,7 +166,9 @@ typedef struct {
  *   B         device, n x R column-major right-hand sides, 1 <= R <= 1024.
  *   n_est     host, R ints in {1, 2}: independent estimators per column (NULL = all 1).  Two
  *             estimators share one CG run and differ only in their uniforms (Sec. 4.1).
- *   S0        device, n x R initial iterates, or NULL for zero.
+ *   S0        device, n x R initial iterates, or NULL for zero.  A column keeps its iterate
+ *             only when ||b - K s_0|| < ||b|| (decided without random draws, so the
+ *             estimates stay unbiased); otherwise it starts from zero.
  *   S_est     device, n x sum(n_est) column-major: the estimators of column 0, then of
  *             column 1, ...
  *   step      counter for the random draws (uniforms for column c, estimator t, step j come
@@ -248,6 +250,71 @@ ulisse_status ulisse_profile_enable(ulisse_ctx *ctx, int enable);
 
 /* Totals since enabling (synchronises the stream); reset != 0 clears them afterwards. */
 ulisse_status ulisse_profile_read(ulisse_ctx *ctx, ulisse_profile *out, int reset);
+
+/*
+ * Learned warm start for the K s = y solve.  Algorithm 1 starts from any iterate s_0, and
+ * the ULISSE estimate stays unbiased for K^{-1} y for every s_0 fixed before the step's
+ * random draws, so a good guess shortens the y solve without biasing the gradient.  The
+ * guess is s_0 = K_s(X, Z) c with Z a seeded subset of the inputs (anchors) and
+ * c = MLP(psi): psi standardised, two tanh layers of `hidden` units, a linear output of
+ * n_anchors.  The network is trained on the GPU on data the chain records as it runs:
+ * at each recorded step's parameters psi_t, n_rows rows I_t drawn uniformly (with
+ * replacement, from a counter-based stream), y at those rows and
+ * M_t = K(X_{I_t}, X; psi_t) K_s(X, Z; psi_t), so that y_{I_t} - M_t c is the solve's
+ * initial residual y - K s_0 on those rows.  Loss
+ * 1/T sum_t (||y_{I_t} - M_t c_t||^2 / m + ridge ||c_t||^2), Adam.  Until the first
+ * training call c = 0 (s_0 = 0, the method without warm start); a solve keeps s_0 only
+ * when it lowers the residual norm below ||y|| (see ulisse_solve).
+ * Device memory: max_pairs * n_rows * n_anchors floats for the recorded M_t, plus
+ * n * n_anchors floats of scratch.
+ */
+typedef struct {
+    int n_anchors;           /* A <= n (512 in the paper-scale configuration) */
+    int hidden;              /* H (256) */
+    int n_rows;              /* m rows per recorded pair, 1..8192 */
+    int max_pairs;           /* capacity of the pair buffer (a ring: the newest are kept) */
+    unsigned long long seed; /* anchors, rows, initial weights and minibatches */
+    double ridge;            /* rho >= 0, weight of ||c||^2 in the loss */
+} ulisse_ws_config;
+
+/* Weights, sampling and recorded pairs, copied to caller-provided HOST buffers (any
+ * pointer may be NULL).  Weights are flattened W1 (p x H), b1, W2 (H x H), b2, W3 (H x A),
+ * b3, each matrix row-major with inputs along rows. */
+typedef struct {
+    float *weights;          /* n_params */
+    int *anchors;            /* A row indices of X */
+    int *pair_rows;          /* max_pairs x m row indices of X */
+    float *mu, *sd;          /* p: input standardisation */
+    float *pair_psi;         /* max_pairs x p */
+    int n_pairs;             /* out: pairs recorded (<= max_pairs) */
+    long long n_params;      /* out */
+} ulisse_ws_state;
+
+/* Allocate the warm start (anchors, rows and weights from cfg->seed; W3 = b3 = 0). */
+ulisse_status ulisse_ws_init(ulisse_ctx *ctx, const ulisse_ws_config *cfg);
+/* record != 0: every gradient / SGLD step appends a pair; use != 0: solves of K s = y
+ * start from the warm start (only after the first training call). */
+ulisse_status ulisse_ws_set(ulisse_ctx *ctx, int record, int use);
+/* Train on the recorded pairs.  First the pooled normal equations of the loss for a
+ * constant c, G c = g with G = sum_t M_t^T M_t / (T m) + ridge I, are formed and G = L L^T
+ * is factorised on the GPU (FP64); the network restarts from that least-squares constant
+ * (W3 = 0, b3 = G^{-1} g) with its output layer whitened, W3 = W~3 L^{-1}, so that the loss
+ * is well conditioned in the coordinates Adam updates.  Then `steps` Adam steps (learning
+ * rate lr, moments restarted) on minibatches of `batch` (<= max_pairs) pairs.  Once eight
+ * or more pairs are recorded, every eighth is held out: minibatches skip it, the held-out
+ * loss is evaluated every 25 steps, and the weights with the lowest held-out loss (the
+ * pooled start included) are kept.  *loss (may be NULL) receives that held-out loss, or the
+ * last minibatch loss without held-out pairs (0 when steps == 0).  batch and lr are not
+ * checked when steps == 0.  Refreshes the BF16 inference weights.
+ * Errors: ULISSE_ERR_BREAKDOWN if G is not numerically positive definite (raise ridge). */
+ulisse_status ulisse_ws_train(ulisse_ctx *ctx, int steps, int batch, double lr, double *loss);
+/* Loss over all recorded pairs and its gradient (host, n_params floats) for the current
+ * weights: the quantity the training kernels descend, exposed for checking. */
+ulisse_status ulisse_ws_loss_grad(ulisse_ctx *ctx, double *loss, float *grad);
+ulisse_status ulisse_ws_export(ulisse_ctx *ctx, ulisse_ws_state *out);
+/* s_0 = K_s(X, Z) MLP(psi) into x0 (device, n floats); bf16 != 0 uses the inference
+ * weights. */
+ulisse_status ulisse_ws_x0(ulisse_ctx *ctx, const double *psi, int bf16, float *x0);
 
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);

@@ -65,6 +65,7 @@ def _load():
             lib.orc_kmv_rows.argtypes = [P, L, I, P, I, P, I, P, L, P]
             lib.orc_kmv_rows_abs.argtypes = [P, L, I, P, I, P, I, P, L, P]
             lib.orc_dkmv_all_rows.argtypes = [P, L, I, P, P, I, P, L, P]
+            lib.orc_cross_signal.argtypes = [P, L, P, L, I, P, P]
             lib.orc_probes.argtypes = [L, I, I, U64, U64, P]
             lib.orc_draw_J.argtypes = [U64, U64, U64, I, D, I]
             lib.orc_draw_J.restype = I
@@ -195,6 +196,18 @@ def omp_threads():
         return int(f())
     except AttributeError:
         return os.cpu_count() or 1
+
+
+def cross_signal(X1, X2, psi):
+    """Signal covariance k_s(x1_a, x2_b) between two point sets (n1 x n2)."""
+    X1 = _f64(X1)
+    X2 = _f64(X2)
+    n1, d = X1.shape
+    n2 = X2.shape[0]
+    psi = _f64(psi)
+    C = np.zeros((n1, n2))
+    _load().orc_cross_signal(_ptr(X1), n1, _ptr(X2), n2, d, _ptr(psi), _ptr(C))
+    return C
 
 
 def dkmv_all(X, psi, V):

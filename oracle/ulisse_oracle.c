@@ -224,6 +224,17 @@ void orc_dkmv_all_rows(const double *X, long n, int d, const double *psi, const 
     }
 }
 
+/* Signal covariance between two point sets: C[a*n2 + b] = k_s(x1_a, x2_b) (n1 x n2,
+ * row-major; no noise term: the points are distinct inputs of the model). */
+void orc_cross_signal(const double *X1, long n1, const double *X2, long n2, int d,
+                      const double *psi, double *C)
+{
+    orc_theta t = unpack(psi, d);
+#pragma omp parallel for schedule(static)
+    for (long a = 0; a < n1; ++a)
+        for (long b = 0; b < n2; ++b) C[a * n2 + b] = k_signal(X1 + a * d, X2 + b * d, &t);
+}
+
 /* All p derivative products in one sweep over the entries:
  * U_all[q] (n x R, col-major, q = 0..p-1) = dK/dpsi_q V. */
 void orc_dkmv_all(const double *X, long n, int d, const double *psi,
@@ -372,14 +383,27 @@ void orc_ulisse_solve(const double *X, long n, int d, const double *psi,
     int off = 0;
     for (int c = 0; c < R; ++c) { est_off[c] = off; off += n_est[c]; }
 
-    /* e_0 = b - K s_0, d_0 = e_0 (Algorithm 1). */
+    /* e_0 = b - K s_0, d_0 = e_0 (Algorithm 1).  A given s_0 is kept for a column only   */
+    /* when ||b - K s_0|| < ||b||; otherwise the column starts from s_0 = 0.  The choice   */
+    /* uses no random draw, so the estimators stay unbiased whichever start is taken.      */
     for (int c = 0; c < R; ++c)
         for (long i = 0; i < n; ++i) s[(long)c * n + i] = S0 ? S0[(long)c * n + i] : 0.0;
     if (S0) orc_kmv(X, n, d, psi, -1, s, R, Kd);
     for (int c = 0; c < R; ++c) {
+        const double *bc = B + (long)c * n;
+        int keep = 0;
+        if (S0) {
+            double rr = 0.0;
+            for (long i = 0; i < n; ++i) {
+                const double r = bc[i] - Kd[(long)c * n + i];
+                rr += r * r;
+            }
+            keep = rr < dot(bc, bc, n);
+        }
         for (long i = 0; i < n; ++i) {
             long k = (long)c * n + i;
-            e[k] = B[k] - (S0 ? Kd[k] : 0.0);
+            if (!keep) s[k] = 0.0;
+            e[k] = B[k] - (keep ? Kd[k] : 0.0);
             dv[k] = e[k];
         }
         ee[c] = dot(e + (long)c * n, e + (long)c * n, n);

@@ -1,5 +1,6 @@
 // C ABI of libulisse (include/ulisse.h): context management and the host-side ordering of
 // the kernels for one K V product, one ULISSE solve, one gradient and one SGLD step.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -8,6 +9,7 @@
 
 #include "../../include/ulisse.h"
 #include "solver_kernels.cuh"
+#include "warm_start.cuh"
 
 using namespace ulisse;
 
@@ -66,6 +68,15 @@ struct ulisse_ctx {
   double entry_rhs = 0.0;
   long long launches = 0;
   std::string err;
+
+  // learned warm start (ulisse_ws_*)
+  bool ws_ready = false, ws_record = false, ws_use = false, ws_trained = false;
+  bool ws_standardized = false;
+  WsBuffers wsb{};
+  int ws_pairs = 0, ws_next = 0, ws_t = 0, ws_loss_blocks = 0;
+  unsigned long long ws_seed = 0, ws_batches = 0;
+  float* ws_c = nullptr;
+  std::vector<void*> ws_allocs;
 
   // event timing of the O(n^2) kernels (ulisse_profile_enable)
   bool prof = false;
@@ -420,11 +431,15 @@ static ulisse_status upload_meta(ulisse_ctx* ctx, int R, const int* n_est, int* 
 
 // Batched CG + ULISSE on columns 0..R-1 of B (S holds s_0 when has_s0).  The host learns
 // the live count after every iteration and launches K V on the live columns only.
+// s0_cols > 0: columns 0..s0_cols-1 of S hold initial iterates (the rest are zero).
 template <typename T>
-static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned long long step) {
-  CgArgs<T> a = cg_args<T>(ctx, has_s0, step);
-  if (has_s0) {
-    CKS(run_kmv(ctx, ctx->S, ctx->iota, R, ctx->KD, ctx->iota, kModeK, -1));
+static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned long long step) {
+  CgArgs<T> a = cg_args<T>(ctx, s0_cols > 0, step);
+  if (s0_cols > 0) {
+    if (s0_cols < R)
+      CK(cudaMemsetAsync((char*)ctx->KD + (size_t)s0_cols * ctx->ldn * ctx->esz, 0,
+                         (size_t)(R - s0_cols) * ctx->ldn * ctx->esz, ctx->stream));
+    CKS(run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1));
     ctx->mvp_rounds += 1;
   }
   cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
@@ -462,10 +477,10 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int has_s0, unsigned lon
   return ULISSE_OK;
 }
 
-static ulisse_status solve_dispatch(ulisse_ctx* ctx, int R, int has_s0,
+static ulisse_status solve_dispatch(ulisse_ctx* ctx, int R, int s0_cols,
                                     unsigned long long step) {
-  return ctx->f64 ? solve_core<double>(ctx, R, has_s0, step)
-                  : solve_core<float>(ctx, R, has_s0, step);
+  return ctx->f64 ? solve_core<double>(ctx, R, s0_cols, step)
+                  : solve_core<float>(ctx, R, s0_cols, step);
 }
 
 // Gradient column maps: left factors SE[0] (a1) and SE[2..1+nr] (z_j) with scales 1/2 and
@@ -569,7 +584,27 @@ static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step) {
   n_est[0] = 2;
   int tot = 0;
   CKS(upload_meta(ctx, R, n_est.data(), &tot));
-  CKS(solve_dispatch(ctx, R, 0, step));
+  int s0_cols = 0;
+  if (ctx->ws_use && ctx->ws_trained) {
+    // learned warm start for the y column; the probe columns start from zero
+    ws_x0(ctx->wsb, ctx->psi_dev, true, (const float*)ctx->xhat, ctx->DP, ctx->n, ctx->params,
+          ctx->ws_c, (float*)ctx->S, ctx->num_sms, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->launches += 2;
+    CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0, (size_t)(R - 1) * ctx->ldn * ctx->esz,
+                       ctx->stream));
+    s0_cols = 1;
+  }
+  CKS(solve_dispatch(ctx, R, s0_cols, step));
+  if (ctx->ws_record) {
+    ws_record(ctx->wsb, ctx->psi_dev, (const float*)ctx->y, (const float*)ctx->xhat, ctx->DP,
+              ctx->params, ctx->ws_next % ctx->wsb.max_pairs, (unsigned long long)ctx->ws_next,
+              ctx->stream);
+    CK(cudaGetLastError());
+    ctx->launches += 4;
+    ctx->ws_next++;
+    ctx->ws_pairs = std::min(ctx->ws_pairs + 1, ctx->wsb.max_pairs);
+  }
   // a2 (second estimate of K^{-1} y) becomes the right factor of the quadratic term.
   CK(cudaMemcpyAsync(ctx->B, (char*)ctx->SE + ctx->ldn * ctx->esz, ctx->ldn * ctx->esz,
                      cudaMemcpyDeviceToDevice, ctx->stream));
@@ -804,7 +839,7 @@ ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, i
   CKS(in_cols(B, ctx->B));
   if (S0) CKS(in_cols(S0, ctx->S));
   CKS(upload_meta(ctx, R, n_est, &tot));
-  CKS(solve_dispatch(ctx, R, S0 ? 1 : 0, step));
+  CKS(solve_dispatch(ctx, R, S0 ? R : 0, step));
   if (!ctx->f64) {
     CK(cudaMemcpy2DAsync(S_est, n * 4, ctx->SE, ctx->ldn * 4, n * 4, tot,
                          cudaMemcpyDeviceToDevice, ctx->stream));
@@ -910,6 +945,285 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
   return status_to_result(ctx, st);
 }
 
+// ---------------------------------------------------------------------------------------
+// Learned warm start
+// ---------------------------------------------------------------------------------------
+static uint64_t splitmix64(uint64_t& x) {
+  uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// k distinct indices of [0, n) (Floyd's sampling), sorted.
+static std::vector<int> sample_distinct(long long n, int k, uint64_t& state) {
+  std::vector<int> out;
+  std::vector<char> used;
+  if (n <= 50000000) used.assign((size_t)n, 0);
+  for (long long j = n - k; j < n; ++j) {
+    const long long t = (long long)(splitmix64(state) % (uint64_t)(j + 1));
+    bool taken = false;
+    if (!used.empty()) taken = used[(size_t)t];
+    else taken = std::find(out.begin(), out.end(), (int)t) != out.end();
+    const long long pick = taken ? j : t;
+    out.push_back((int)pick);
+    if (!used.empty()) used[(size_t)pick] = 1;
+  }
+  std::sort(out.begin(), out.end());
+  return out;
+}
+
+static ulisse_status ws_alloc(ulisse_ctx* ctx, void** p, size_t bytes) {
+  CKS(dev_alloc(ctx, p, bytes));
+  ctx->ws_allocs.push_back(*p);
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_init(ulisse_ctx* ctx, const ulisse_ws_config* cfg) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!cfg) return fail(ctx, ULISSE_ERR_ARG, "cfg is null");
+  if (ctx->f64) return fail(ctx, ULISSE_ERR_ARG, "the warm start needs an FP32 or mixed context");
+  if (ctx->ws_ready) return fail(ctx, ULISSE_ERR_ARG, "warm start already initialised");
+  const int A = cfg->n_anchors, H = cfg->hidden, m = cfg->n_rows, P = cfg->max_pairs;
+  const int d = ctx->d, p = d + 2;
+  if (A < 1 || A > ctx->n || H < 1 || H > 4096 || m < 1 || m > 8192 || P < 1 ||
+      (long long)A * (ctx->DP + 1) > 12288 || !(cfg->ridge >= 0.0) || !std::isfinite(cfg->ridge))
+    return fail(ctx, ULISSE_ERR_ARG, "warm start sizes out of range");
+  WsBuffers& b = ctx->wsb;
+  b.p = p; b.H = H; b.A = A; b.m = m; b.max_pairs = P; b.d = d; b.n = ctx->n;
+  b.ridge = (float)cfg->ridge;
+  b.seed = cfg->seed;
+  ctx->ws_seed = cfg->seed;
+  uint64_t st = cfg->seed ^ 0x5A17A11CE0FF5E75ull;
+  const std::vector<int> anch = sample_distinct(ctx->n, A, st);
+  {
+    // split the j range of the recording product so that about two CTAs run per SM
+    const long long tiles = (long long)((A + 63) / 64) * ((m + 63) / 64);
+    long long ns = std::max<long long>(1, (2LL * ctx->num_sms + tiles - 1) / tiles);
+    ns = std::min<long long>(ns, std::max<long long>(1, ctx->n / 256));
+    b.n_split = (int)std::min<long long>(ns, 32);
+  }
+  const long long np = ws_param_count(p, H, A);
+  std::vector<float> w((size_t)np, 0.f);
+  auto normal = [&]() {
+    const double u1 = ((splitmix64(st) >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+    const double u2 = (splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  for (long long k = 0; k < (long long)p * H; ++k) w[k] = (float)(normal() / std::sqrt((double)p));
+  const long long oW2 = (long long)p * H + H;
+  for (long long k = 0; k < (long long)H * H; ++k) w[oW2 + k] = (float)(normal() / std::sqrt((double)H));
+  const int nlb = ws_loss_blocks(m);
+  ctx->ws_loss_blocks = nlb;
+  void* q = nullptr;
+#define WSA(field, bytes) do { CKS(ws_alloc(ctx, &q, (bytes))); b.field = reinterpret_cast<decltype(b.field)>(q); } while (0)
+  WSA(anch, sizeof(int) * A);
+  WSA(w, sizeof(float) * np);
+  WSA(g, sizeof(float) * np);
+  WSA(adam_m, sizeof(float) * np);
+  WSA(adam_v, sizeof(float) * np);
+  WSA(wb, sizeof(__nv_bfloat16) * np);
+  WSA(pair_psi, sizeof(float) * (size_t)P * p);
+  WSA(pair_rows, sizeof(int) * (size_t)P * m);
+  WSA(pair_y, sizeof(float) * (size_t)P * m);
+  WSA(pair_M, sizeof(float) * (size_t)P * m * A);
+  WSA(cross, sizeof(float) * (size_t)ctx->n * A);
+  WSA(Mpart, sizeof(float) * (size_t)b.n_split * m * A);
+  WSA(mu, sizeof(float) * p);
+  WSA(sd, sizeof(float) * p);
+  WSA(idx, sizeof(int) * P);
+  WSA(Z, sizeof(float) * (size_t)P * p);
+  WSA(H1, sizeof(float) * (size_t)P * H);
+  WSA(H2, sizeof(float) * (size_t)P * H);
+  WSA(dH, sizeof(float) * (size_t)P * H);
+  WSA(dA, sizeof(float) * (size_t)P * H);
+  WSA(C, sizeof(float) * (size_t)P * A);
+  WSA(dC, sizeof(float) * (size_t)P * A);
+  WSA(R, sizeof(float) * (size_t)P * m);
+  WSA(loss_part, sizeof(double) * (size_t)P * nlb);
+  WSA(G, sizeof(double) * (size_t)A * A);
+  WSA(Ginv, sizeof(double) * (size_t)A * A);
+  WSA(gb, sizeof(double) * (size_t)A);
+  WSA(P, sizeof(float) * (size_t)A * A);
+  WSA(gbf, sizeof(float) * (size_t)A);
+  WSA(wt, sizeof(float) * (size_t)(H + 1) * A);
+  WSA(gt, sizeof(float) * (size_t)(H + 1) * A);
+  WSA(flag, sizeof(int));
+  WSA(w_best, sizeof(float) * np);
+  WSA(wt_best, sizeof(float) * (size_t)(H + 1) * A);
+#undef WSA
+  CKS(ws_alloc(ctx, &q, sizeof(float) * A));
+  ctx->ws_c = static_cast<float*>(q);
+  CK(cudaMemcpyAsync(b.anch, anch.data(), sizeof(int) * A, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(b.w, w.data(), sizeof(float) * np, cudaMemcpyHostToDevice, ctx->stream));
+  std::vector<float> ones(p, 1.f);
+  CK(cudaMemcpyAsync(b.sd, ones.data(), sizeof(float) * p, cudaMemcpyHostToDevice, ctx->stream));
+  ws_to_bf16(b, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ws_ready = true;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_set(ulisse_ctx* ctx, int record, int use) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!ctx->ws_ready) return fail(ctx, ULISSE_ERR_ARG, "warm start not initialised");
+  ctx->ws_record = record != 0;
+  ctx->ws_use = use != 0;
+  return ULISSE_OK;
+}
+
+static ulisse_status ws_sum_loss(ulisse_ctx* ctx, int B, double* loss) {
+  std::vector<double> parts((size_t)B * ctx->ws_loss_blocks);
+  CK(cudaMemcpyAsync(parts.data(), ctx->wsb.loss_part, sizeof(double) * parts.size(),
+                     cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  double t = 0.0;
+  for (double v : parts) t += v;
+  if (loss) *loss = t / ((double)B * ctx->wsb.m);
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_train(ulisse_ctx* ctx, int steps, int batch, double lr, double* loss) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!ctx->ws_ready || ctx->ws_pairs < 1)
+    return fail(ctx, ULISSE_ERR_ARG, "no recorded pairs to train on");
+  if (steps < 0 || (steps > 0 && (batch < 1 || batch > ctx->wsb.max_pairs || !(lr > 0.0) ||
+                                  !std::isfinite(lr))))
+    return fail(ctx, ULISSE_ERR_ARG, "bad training arguments");
+  WsBuffers& b = ctx->wsb;
+  const int T = ctx->ws_pairs;
+  ws_standardize(b, T, ctx->stream);
+  ctx->ws_standardized = true;
+  // Start from the pooled least-squares constant with the output layer whitened, then take
+  // Adam steps in the whitened coordinates (moments restart with each call).
+  if (!ws_whiten(b, T, ctx->stream)) {
+    CK(cudaGetLastError());
+    return fail(ctx, ULISSE_ERR_BREAKDOWN,
+                "warm start: pooled normal matrix is not positive definite (raise ridge)");
+  }
+  CK(cudaGetLastError());
+  ctx->launches += 6;
+  const long long np = ws_param_count(b.p, b.H, b.A);
+  const long long nl = (long long)(b.H + 1) * b.A;
+  CK(cudaMemsetAsync(b.adam_m, 0, sizeof(float) * np, ctx->stream));
+  CK(cudaMemsetAsync(b.adam_v, 0, sizeof(float) * np, ctx->stream));
+  ctx->ws_t = 0;
+  // Every eighth pair is held out once there are at least eight: minibatches come from the
+  // rest, and the weights with the lowest held-out loss (the pooled start included) are kept.
+  std::vector<int> train, val;
+  for (int t = 0; t < T; ++t) ((T >= 8 && t % 8 == 7) ? val : train).push_back(t);
+  const bool validate = !val.empty() && steps > 0;
+  auto val_loss = [&](double* out) -> ulisse_status {
+    CK(cudaMemcpyAsync(b.idx, val.data(), sizeof(int) * val.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ws_loss_grad(b, (int)val.size(), ctx->ws_loss_blocks, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->launches += 16;
+    return ws_sum_loss(ctx, (int)val.size(), out);
+  };
+  auto save_best = [&]() -> ulisse_status {
+    CK(cudaMemcpyAsync(b.w_best, b.w, sizeof(float) * np, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(b.wt_best, b.wt, sizeof(float) * nl, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    return ULISSE_OK;
+  };
+  double best = 0.0, cur = 0.0, last = 0.0;
+  if (validate) {
+    CKS(val_loss(&best));
+    CKS(save_best());
+  }
+  constexpr int kEvalEvery = 25;
+  std::vector<int> idx(std::max(batch, 1));
+  for (int it = 0; it < steps; ++it) {
+    uint64_t st = ctx->ws_seed ^ (0xB5AD4ECEDA1CE2A9ull * (++ctx->ws_batches));
+    for (int k = 0; k < batch; ++k)
+      idx[k] = train[(size_t)(splitmix64(st) % (uint64_t)train.size())];
+    CK(cudaMemcpyAsync(b.idx, idx.data(), sizeof(int) * batch, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ws_loss_grad(b, batch, ctx->ws_loss_blocks, ctx->stream);
+    ws_adam_whitened(b, (float)lr, ++ctx->ws_t, ctx->stream);
+    CK(cudaGetLastError());
+    ctx->launches += 20;
+    if (!validate && it == steps - 1) CKS(ws_sum_loss(ctx, batch, &last));
+    if (validate && ((it + 1) % kEvalEvery == 0 || it == steps - 1)) {
+      CKS(val_loss(&cur));
+      if (cur < best) {
+        best = cur;
+        CKS(save_best());
+      }
+    }
+  }
+  if (validate) {
+    CK(cudaMemcpyAsync(b.w, b.w_best, sizeof(float) * np, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(b.wt, b.wt_best, sizeof(float) * nl, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+  }
+  if (loss) *loss = validate ? best : last;
+  ws_to_bf16(b, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->ws_trained = true;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_loss_grad(ulisse_ctx* ctx, double* loss, float* grad) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!ctx->ws_ready || ctx->ws_pairs < 1)
+    return fail(ctx, ULISSE_ERR_ARG, "no recorded pairs");
+  WsBuffers& b = ctx->wsb;
+  if (!ctx->ws_standardized) {
+    ws_standardize(b, ctx->ws_pairs, ctx->stream);
+    ctx->ws_standardized = true;
+  }
+  const int T = ctx->ws_pairs;
+  std::vector<int> idx(T);
+  for (int k = 0; k < T; ++k) idx[k] = k;
+  CK(cudaMemcpyAsync(b.idx, idx.data(), sizeof(int) * T, cudaMemcpyHostToDevice, ctx->stream));
+  ws_loss_grad(b, T, ctx->ws_loss_blocks, ctx->stream);
+  CK(cudaGetLastError());
+  CKS(ws_sum_loss(ctx, T, loss));
+  if (grad)
+    CK(cudaMemcpyAsync(grad, b.g, sizeof(float) * ws_param_count(b.p, b.H, b.A),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_export(ulisse_ctx* ctx, ulisse_ws_state* out) {
+  if (!ctx || !out) return ULISSE_ERR_ARG;
+  if (!ctx->ws_ready) return fail(ctx, ULISSE_ERR_ARG, "warm start not initialised");
+  const WsBuffers& b = ctx->wsb;
+  const long long np = ws_param_count(b.p, b.H, b.A);
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> ulisse_status {
+    if (dst) CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return ULISSE_OK;
+  };
+  CKS(cp(out->weights, b.w, sizeof(float) * np));
+  CKS(cp(out->anchors, b.anch, sizeof(int) * b.A));
+
+  CKS(cp(out->mu, b.mu, sizeof(float) * b.p));
+  CKS(cp(out->sd, b.sd, sizeof(float) * b.p));
+  CKS(cp(out->pair_psi, b.pair_psi, sizeof(float) * (size_t)b.max_pairs * b.p));
+  CKS(cp(out->pair_rows, b.pair_rows, sizeof(int) * (size_t)b.max_pairs * b.m));
+  CK(cudaStreamSynchronize(ctx->stream));
+  out->n_pairs = ctx->ws_pairs;
+  out->n_params = np;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_ws_x0(ulisse_ctx* ctx, const double* psi, int bf16, float* x0) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (!ctx->ws_ready || !x0) return fail(ctx, ULISSE_ERR_ARG, "warm start not initialised or x0 null");
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  ws_x0(ctx->wsb, ctx->psi_dev, bf16 != 0, (const float*)ctx->xhat, ctx->DP, ctx->n, ctx->params,
+        ctx->ws_c, x0, ctx->num_sms, ctx->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ULISSE_OK;
+}
+
 ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,
                               long long* kernel_launches) {
   if (!ctx) return ULISSE_ERR_ARG;
@@ -960,6 +1274,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->M_dev), reinterpret_cast<void**>(&ctx->prior_dev),
                    reinterpret_cast<void**>(&ctx->status_dev)})
     dev_free(*p);
+  for (void* p : ctx->ws_allocs) cudaFree(p);
+  ctx->ws_allocs.clear();
   prof_drain(ctx);
   for (auto& e : ctx->free_events) {
     cudaEventDestroy(e.first);

@@ -85,15 +85,28 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   T* d = a.D + c * a.ld;
   const T* b = a.B + c * a.ld;
   const T* ks0 = a.KD + c * a.ld;
-  double p = 0.0;
+  // An initial iterate is kept only when it lowers the residual norm below that of s_0 = 0.
+  // The choice depends on the parameters, the data and the iterate alone (no random draw),
+  // so every estimator built on it stays unbiased.
+  double pb = 0.0, pr = 0.0;
   for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
-    if (!a.has_s0) s[i] = T(0);
-    const T ei = a.has_s0 ? b[i] - ks0[i] : b[i];
+    const double bi = (double)b[i];
+    pb += bi * bi;
+    if (a.has_s0) {
+      const double ri = (double)(T)(b[i] - ks0[i]);
+      pr += ri * ri;
+    }
+  }
+  const double bb = block_sum<kCgNT>(pb, red);
+  const double rr = a.has_s0 ? block_sum<kCgNT>(pr, red) : bb;
+  const bool keep = a.has_s0 && rr < bb;
+  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
+    if (!keep) s[i] = T(0);
+    const T ei = keep ? b[i] - ks0[i] : b[i];
     e[i] = ei;
     d[i] = ei;
-    p += (double)ei * (double)ei;
   }
-  const double ee = block_sum<kCgNT>(p, red);
+  const double ee = keep ? rr : bb;
   const int n_est = st.n_est;
   const bool done = sqrt(ee) < a.eps;
   if (done) {

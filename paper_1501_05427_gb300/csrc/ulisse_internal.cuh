@@ -24,6 +24,7 @@ constexpr int kStatusBadM = 8;
 constexpr uint64_t kPurposeProbe = 1;
 constexpr uint64_t kPurposeUlisse = 2;
 constexpr uint64_t kPurposeSgld = 3;
+constexpr uint64_t kPurposeWsRows = 4;
 
 // Scalars derived from psi on the device (written by the prescale kernel).
 struct DevParams {

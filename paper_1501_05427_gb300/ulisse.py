@@ -31,7 +31,8 @@ EXPORTED = [
     "ulisse_config_default", "ulisse_create", "ulisse_create_host", "ulisse_kmv",
     "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
     "ulisse_counters", "ulisse_profile_enable", "ulisse_profile_read", "ulisse_last_error",
-    "ulisse_destroy", "ulisse_kmv_noalloc",
+    "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
+    "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0",
 ]
 
 
@@ -60,6 +61,19 @@ class ulisse_profile(ctypes.Structure):
     _fields_ = [("kmv_launches", ctypes.c_longlong), ("kmv_ms", ctypes.c_double),
                 ("kmv_flop", ctypes.c_double), ("grad_launches", ctypes.c_longlong),
                 ("grad_ms", ctypes.c_double), ("grad_flop", ctypes.c_double)]
+
+
+class ulisse_ws_config(ctypes.Structure):
+    _fields_ = [("n_anchors", ctypes.c_int), ("hidden", ctypes.c_int), ("n_rows", ctypes.c_int),
+                ("max_pairs", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("ridge", ctypes.c_double)]
+
+
+class ulisse_ws_state(ctypes.Structure):
+    _fields_ = [("weights", ctypes.c_void_p), ("anchors", ctypes.c_void_p),
+                ("pair_rows", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("sd", ctypes.c_void_p),
+                ("pair_psi", ctypes.c_void_p), ("n_pairs", ctypes.c_int),
+                ("n_params", ctypes.c_longlong)]
 
 
 class UlisseError(RuntimeError):
@@ -99,6 +113,12 @@ def load():
     lib.ulisse_profile_enable.argtypes = [P, I]
     lib.ulisse_profile_read.argtypes = [P, ctypes.POINTER(ulisse_profile), I]
     lib.ulisse_kmv_noalloc.argtypes = [P, LL, I, P, I, P, I, P, P]
+    lib.ulisse_ws_init.argtypes = [P, ctypes.POINTER(ulisse_ws_config)]
+    lib.ulisse_ws_set.argtypes = [P, I, I]
+    lib.ulisse_ws_train.argtypes = [P, I, I, D, ctypes.POINTER(D)]
+    lib.ulisse_ws_loss_grad.argtypes = [P, ctypes.POINTER(D), P]
+    lib.ulisse_ws_export.argtypes = [P, ctypes.POINTER(ulisse_ws_state)]
+    lib.ulisse_ws_x0.argtypes = [P, P, I, P]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -256,6 +276,50 @@ class Context:
         self._check(st, allow)
         return psi_dev
 
+    # -- learned warm start --------------------------------------------------------------
+    def ws_init(self, n_anchors=512, hidden=256, n_rows=1024, max_pairs=256, seed=0,
+                ridge=1e-2):
+        cfg = ulisse_ws_config(n_anchors, hidden, n_rows, max_pairs, seed, ridge)
+        self._check(self._lib.ulisse_ws_init(self._h, ctypes.byref(cfg)))
+        self.ws_cfg = cfg
+
+    def ws_set(self, record=False, use=False):
+        self._check(self._lib.ulisse_ws_set(self._h, int(bool(record)), int(bool(use))))
+
+    def ws_train(self, steps, batch=64, lr=1e-3):
+        loss = ctypes.c_double()
+        self._check(self._lib.ulisse_ws_train(self._h, steps, batch, lr, ctypes.byref(loss)))
+        return loss.value
+
+    def ws_loss_grad(self):
+        st = self.ws_export()
+        g = np.zeros(st["n_params"], dtype=np.float32)
+        loss = ctypes.c_double()
+        self._check(self._lib.ulisse_ws_loss_grad(self._h, ctypes.byref(loss), _hptr(g)))
+        return loss.value, g
+
+    def ws_export(self):
+        cfg = self.ws_cfg
+        p, H, A, m, P = self.p, cfg.hidden, cfg.n_anchors, cfg.n_rows, cfg.max_pairs
+        npar = p * H + H + H * H + H + H * A + A
+        out = dict(weights=np.zeros(npar, np.float32), anchors=np.zeros(A, np.int32),
+                   pair_rows=np.zeros((P, m), np.int32), mu=np.zeros(p, np.float32),
+                   sd=np.zeros(p, np.float32), pair_psi=np.zeros((P, p), np.float32))
+        st = ulisse_ws_state(*[_hptr(out[k]) for k in ("weights", "anchors", "pair_rows", "mu",
+                                                       "sd", "pair_psi")], 0, 0)
+        self._check(self._lib.ulisse_ws_export(self._h, ctypes.byref(st)))
+        out["n_pairs"] = st.n_pairs
+        out["n_params"] = st.n_params
+        return out
+
+    def ws_x0(self, psi, bf16=False):
+        import torch
+        x0 = torch.empty(self.n, dtype=torch.float32, device="cuda")
+        psi = _f64_host(psi, self.p)
+        self._check(self._lib.ulisse_ws_x0(self._h, _hptr(psi), int(bool(bf16)),
+                                           ctypes.c_void_p(x0.data_ptr())))
+        return x0
+
     def counters(self):
         """(K V rounds, generated entries x right-hand sides, kernel launches) so far."""
         a = ctypes.c_longlong()
@@ -339,6 +403,30 @@ def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
     if st != ULISSE_OK:
         raise UlisseError(st, "ulisse_kmv_noalloc rejected the call")
     return out[:, 0] if V.dim() == 1 else out
+
+
+def ulisse_ws_init(ctx: Context, **kw):
+    ctx.ws_init(**kw)
+
+
+def ulisse_ws_set(ctx: Context, record=False, use=False):
+    ctx.ws_set(record, use)
+
+
+def ulisse_ws_train(ctx: Context, steps, batch=64, lr=1e-3):
+    return ctx.ws_train(steps, batch, lr)
+
+
+def ulisse_ws_loss_grad(ctx: Context):
+    return ctx.ws_loss_grad()
+
+
+def ulisse_ws_export(ctx: Context):
+    return ctx.ws_export()
+
+
+def ulisse_ws_x0(ctx: Context, psi, bf16=False):
+    return ctx.ws_x0(psi, bf16)
 
 
 def ulisse_destroy(ctx: Context):

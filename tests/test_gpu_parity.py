@@ -236,6 +236,37 @@ def test_solve_parity_fp64(orc, n, d, R, q):
                     q, 1e-6)
 
 
+def test_solve_initial_iterates_fp64(orc):
+    """Columns with a good initial iterate (kept), a bad one (dropped: zero start) and none:
+    the keep decision and the trajectories follow the oracle."""
+    prob = w.small_2d(n=400)
+    n = prob.n
+    rng = np.random.default_rng(3)
+    B = rng.standard_normal((n, 3)).astype(np.float32)
+    B[:, 0] = prob.y
+    Xd = prob.X.astype(np.float64)
+    good = orc.exact_solve(Xd, prob.psi_true, B[:, 0].astype(np.float64))
+    good = good + 0.02 * np.std(good) * rng.standard_normal(n)
+    S0 = np.stack([good, 30.0 * rng.standard_normal(n), np.zeros(n)], axis=1).astype(np.float32)
+    Sref, st_ref = orc.ulisse_solve(Xd, prob.psi_true, B.astype(np.float64),
+                                    S0=S0.astype(np.float64), q=0.1, max_iter=300, seed=5, step=1)
+    Sz, st_z = orc.ulisse_solve(Xd, prob.psi_true, B.astype(np.float64), q=0.1, max_iter=300,
+                                seed=5, step=1)
+    assert st_ref[0, 1] < st_z[0, 1]                       # the kept start saves iterations
+    assert np.array_equal(Sref[:, 1:], Sz[:, 1:])          # the dropped one changes nothing
+    with _ctx(prob, precision=u.PREC_FP64, q=0.1, max_iter=300, seed=5) as ctx:
+        Sg, st = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(),
+                           S0=torch.from_numpy(S0).cuda(), step=1)
+        Sg0, _ = ctx.solve(prob.psi_true, torch.from_numpy(B).cuda(), step=1)
+    for c in range(3):
+        assert tuple(st[c][:4]) == tuple(int(v) for v in st_ref[c, :4])
+    Sg = Sg.cpu().numpy().astype(np.float64)
+    # the kept start: 5 FP64 iterations, the GPU follows the oracle's trajectory
+    assert np.max(np.abs(Sg[:, 0] - Sref[:, 0])) <= 2e-6 * np.max(np.abs(Sref[:, 0]))
+    # the dropped starts: exactly the GPU's own zero-start solve
+    assert np.array_equal(Sg[:, 1:], Sg0.cpu().numpy().astype(np.float64)[:, 1:])
+
+
 def test_solve_fp64_matches_oracle_tightly(orc):
     prob = w.small_2d(n=400)
     B = np.random.default_rng(2).standard_normal((400, 3)).astype(np.float32)

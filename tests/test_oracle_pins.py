@@ -22,11 +22,19 @@ a wrong sign or index, a transposed operand, a wrong weight) fails at least one 
                         vs the paper's printed 1.4 at beta = 1 (tests/golden)
   ulisse_solve          reconstruction from the recorded CG trajectory; exact expectation by
                         enumerating J equals the converged CG solution; mean of 10^4 seeded
-                        estimates within 4 SE (exact covariance) of the Cholesky solution
+                        estimates within 4 SE (exact covariance) of the Cholesky solution;
+                        a worse initial iterate gives the zero-start result bit for bit, a
+                        kept one is reconstructed from its own trajectory
   grad_estimate         mean of 10^4 seeded estimates within 4 SE of the exact gradient;
                         Hutchinson identity by enumerating all sign vectors
   chol / sgld_update    numpy.linalg.cholesky; closed-form update with the drawn noise;
                         stationary moments of a Gaussian target
+  cross_signal          sub-block of cov_matrix (signal part) for a subset of the inputs
+  mlp.residual_matrices y_I - M c equals the rows I of y - K s_0 with dense K
+  mlp.loss_and_grad     central finite differences of the loss in every parameter block;
+                        the loss at a hand-built exact fit is 0, the ridge term alone
+  mlp.pooled_constant   the loss gradient in b3 vanishes there (W3 = 0), and any other
+                        constant has a larger loss
 """
 import math
 import os
@@ -388,6 +396,52 @@ def test_ulisse_unbiased_statistical(orc):
     assert st[:, 1].mean() < T
 
 
+def test_ulisse_initial_iterate_rule(orc):
+    """An initial iterate s_0 is kept only when ||b - K s_0|| < ||b||.  A worse one gives
+    exactly the zero-start estimates; a kept one starts CG (Algorithm 1) from s_0, and the
+    expectation over the law of J, enumerated exactly, is still the solution of K s = b."""
+    n = 40
+    X = _rand_X(n, 2, 13)
+    psi = np.log([0.3, 0.3, 1.0, 0.3])
+    b = np.random.default_rng(13).standard_normal(n)
+    q, beta, eps = 0.5, 1.0, 1e-11
+    exact = orc.exact_solve(X, psi, b)
+    R = 64
+    B = np.repeat(b[:, None], R, axis=1)
+    kw = dict(colid=np.arange(R), q=q, beta=beta, eps=eps, seed=6, step=2)
+    S_zero, st_zero = orc.ulisse_solve(X, psi, B, **kw)
+    bad = 50.0 * np.random.default_rng(14).standard_normal((n, R))
+    S_bad, st_bad = orc.ulisse_solve(X, psi, B, S0=bad, **kw)
+    assert np.array_equal(S_bad, S_zero) and np.array_equal(st_bad, st_zero)
+
+    s0 = exact + 0.05 * np.linalg.norm(exact) / math.sqrt(n) * \
+        np.random.default_rng(15).standard_normal(n)
+    K = orc.cov_matrix(X, psi)
+    assert np.linalg.norm(b - K @ s0) < np.linalg.norm(b)
+    tr = orc.cg_record(X, psi, b, s0=s0, eps=eps)
+    S, T = tr["S"], tr["T"]
+    delta = np.diff(S, axis=0)
+    norms = np.linalg.norm(tr["E"], axis=1)
+    l = next(i for i in range(1, T + 1) if norms[i] < q * math.sqrt(n))
+    S_est, st = orc.ulisse_solve(X, psi, B, S0=np.repeat(s0[:, None], R, axis=1), **kw)
+    for c in range(R):
+        J = int(st[c, 3])
+        assert st[c, 0] == l
+        ref = S[l].copy()
+        for j in range(1, min(J, T - l) + 1):
+            ref += orc.weight_product(j, beta) * delta[l + j - 1]
+        assert np.linalg.norm(S_est[:, c] - ref) < 1e-9 * np.linalg.norm(ref)
+    mean = np.zeros(n)
+    for J in range(0, T - l + 1):
+        pJ = math.exp(-beta * J * (J + 1) / 2) - (math.exp(-beta * (J + 1) * (J + 2) / 2)
+                                                  if J < T - l else 0.0)
+        est = S[l].copy()
+        for j in range(1, J + 1):
+            est += orc.weight_product(j, beta) * delta[l + j - 1]
+        mean += pJ * est
+    assert np.linalg.norm(mean - exact) < 1e-7 * np.linalg.norm(exact)
+
+
 def test_hutchinson_identity_exhaustive(orc):
     """Sec. 2.1: E[r^T A r] = Tr(A) for +-1 probes, checked by enumerating all 2^n vectors."""
     n = 10
@@ -505,3 +559,92 @@ def test_sgld_stationary_gaussian(orc):
     for i in range(2):
         se_var = Sigma[i, i] * math.sqrt(2 / ess)
         assert abs(C[i, i] - Sigma[i, i]) < 4 * se_var + 2 * eps_t * Sigma[i, i]
+
+
+# ----------------------------------------------------------------------------------------
+# Learned warm start (oracle/mlp.py)
+# ----------------------------------------------------------------------------------------
+def test_cross_signal_is_covariance_block(orc):
+    X = _rand_X(30, 3, 50)
+    psi = np.log([0.4, 0.7, 0.5, 1.3, 0.2])
+    K = orc.cov_matrix(X, psi) - 0.2 * np.eye(30)
+    idx = [3, 7, 21, 29]
+    C = orc.cross_signal(X, X[idx], psi)
+    assert np.max(np.abs(C - K[:, idx])) < 1e-14
+
+
+def _mlp_case(seed=0, p=4, hidden=7, A=5, m=6, T=3, n=12):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(0, 1, (n, p - 2))
+    y = rng.standard_normal(n)
+    Z = X[rng.choice(n, A, replace=False)]
+    Rows = rng.integers(0, n, (T, m))
+    Psi = np.log([0.4, 0.5, 1.0, 0.1]) + 0.1 * rng.standard_normal((T, p))
+    w = 0.3 * rng.standard_normal(sum(int(np.prod(s)) for s in mlp.shapes(p, hidden, A)))
+    mu = Psi.mean(axis=0)
+    sd = Psi.std(axis=0) + 1e-3
+    return mlp, w, Psi, Rows, X, y, Z, mu, sd, hidden
+
+
+def test_mlp_residual_matrices_are_initial_residual_rows(orc):
+    """y_I - M c is the initial residual y - K s_0 of Algorithm 1 at s_0 = K_s(X, Z) c, on
+    the rows I (dense K from cov_matrix)."""
+    mlp, w, Psi, Rows, X, y, Z, mu, sd, hidden = _mlp_case(seed=3)
+    M = mlp.residual_matrices(X, Rows, Z, Psi)
+    c = np.random.default_rng(4).standard_normal(Z.shape[0])
+    for t, psi in enumerate(Psi):
+        K = orc.cov_matrix(X, psi)
+        s0 = orc.cross_signal(X, Z, psi) @ c
+        ref = (y - K @ s0)[Rows[t]]
+        assert np.allclose(y[Rows[t]] - M[t] @ c, ref, rtol=0, atol=1e-12 * np.max(np.abs(ref)))
+
+
+def test_mlp_gradient_vs_finite_differences(orc):
+    mlp, w, Psi, Rows, X, y, Z, mu, sd, hidden = _mlp_case()
+    M = mlp.residual_matrices(X, Rows, Z, Psi)
+    ridge = 0.01
+    loss, g = mlp.loss_and_grad(w, Psi, Rows, X, y, Z, mu, sd, hidden, ridge)
+    h = 1e-6
+    rng = np.random.default_rng(1)
+    idx = rng.choice(len(w), 40, replace=False)
+    # every parameter block is represented
+    sizes = np.cumsum([int(np.prod(s)) for s in mlp.shapes(4, hidden, 5)])
+    idx = np.unique(np.concatenate([idx, sizes - 1]))
+    for k in idx:
+        wp, wm = w.copy(), w.copy()
+        wp[k] += h
+        wm[k] -= h
+        fd = (mlp.loss_and_grad(wp, Psi, Rows, X, y, Z, mu, sd, hidden, ridge, M=M)[0] -
+              mlp.loss_and_grad(wm, Psi, Rows, X, y, Z, mu, sd, hidden, ridge, M=M)[0]) / (2 * h)
+        assert abs(fd - g[k]) < 1e-7 * max(1.0, abs(fd)), (k, fd, g[k])
+
+
+def test_mlp_exact_fit_has_zero_loss(orc):
+    """With W3 = 0 the network outputs c = b3; data y = K K_s(X, Z) b3 at the pair's
+    parameters has a zero initial residual, so the loss (ridge 0) and its gradient vanish."""
+    mlp, w, Psi, Rows, X, _, Z, mu, sd, hidden = _mlp_case(seed=2, T=1)
+    W1, b1, W2, b2, W3, b3 = mlp.unflatten(w, 4, hidden, 5)
+    w0 = mlp.flatten([W1, b1, W2, b2, np.zeros_like(W3), b3])
+    y = orc.cov_matrix(X, Psi[0]) @ (orc.cross_signal(X, Z, Psi[0]) @ b3)
+    loss, g = mlp.loss_and_grad(w0, Psi, Rows, X, y, Z, mu, sd, hidden, 0.0)
+    assert loss < 1e-26 and np.max(np.abs(g)) < 1e-12
+    # the ridge term alone: rho ||b3||^2
+    loss_r, _ = mlp.loss_and_grad(w0, Psi, Rows, X, y, Z, mu, sd, hidden, 0.5)
+    assert abs(loss_r - 0.5 * np.sum(b3 * b3)) < 1e-12
+
+
+def test_mlp_pooled_constant_is_the_loss_minimiser(orc):
+    mlp, w, Psi, Rows, X, y, Z, mu, sd, hidden = _mlp_case(seed=5, T=4, m=9)
+    ridge = 0.05
+    M = mlp.residual_matrices(X, Rows, Z, Psi)
+    c = mlp.pooled_constant(M, y[Rows], ridge)
+    W1, b1, W2, b2, W3, b3 = mlp.unflatten(w, 4, hidden, 5)
+    w0 = mlp.flatten([W1, b1, W2, b2, np.zeros_like(W3), c])
+    loss, g = mlp.loss_and_grad(w0, Psi, Rows, X, y, Z, mu, sd, hidden, ridge, M=M)
+    gb3 = g[-5:]
+    assert np.max(np.abs(gb3)) < 1e-12 * max(1.0, np.max(np.abs(c)))
+    rng = np.random.default_rng(6)
+    for _ in range(5):
+        w1 = mlp.flatten([W1, b1, W2, b2, np.zeros_like(W3), c + 0.01 * rng.standard_normal(5)])
+        assert mlp.loss_and_grad(w1, Psi, Rows, X, y, Z, mu, sd, hidden, ridge, M=M)[0] > loss
