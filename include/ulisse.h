@@ -316,6 +316,47 @@ ulisse_status ulisse_ws_export(ulisse_ctx *ctx, ulisse_ws_state *out);
  * weights. */
 ulisse_status ulisse_ws_x0(ulisse_ctx *ctx, const double *psi, int bf16, float *x0);
 
+/*
+ * Batched contexts: many independent GP problems of uneven size (Sec. 2's problem, once per
+ * data set), advanced together.  Each problem b keeps its own data, parameters psi_b
+ * (p_b = d_b + 2) and solver state, and draws from its own random streams (the generator
+ * key is cfg->seed + b, so problem b reproduces a single context created with that seed).
+ * The O(n^2) passes of all problems run as ONE persistent launch each: every CG round's
+ * covariance products over all live columns of all problems, and the fused gradient
+ * sweep; the work list has one item per (problem, 256-row block), longest rows first.
+ * Parameters and gradients are packed: problem b's p_b values follow problem b-1's.
+ * Batched contexts run the FP32 path (cfg->precision must be ULISSE_PREC_FP32), take
+ * n_probes <= 16, and accept only the ulisse_batch_* calls (plus counters and destroy);
+ * the single-problem calls return ULISSE_ERR_ARG on them.
+ *
+ *   n_problems  1 .. 4096.   n, d: host arrays of n_problems sizes (1 <= d_b <= 8).
+ *   X, y        host arrays of n_problems DEVICE pointers (row-major n_b x d_b, and n_b);
+ *               copied into the context.
+ * Errors: ULISSE_ERR_ARG (bad sizes, null pointers, precision), ULISSE_ERR_NOMEM.
+ */
+ulisse_status ulisse_create_batched(ulisse_ctx **out, int n_problems, const long long *n,
+                                    const int *d, const float *const *X, const float *const *y,
+                                    const ulisse_config *cfg, void *stream);
+
+/* Number of problems and total packed parameter count (n_params may be NULL). */
+ulisse_status ulisse_batch_size(const ulisse_ctx *ctx, int *n_problems, int *n_params);
+
+/* U_b = K_b(psi_b) V_b for every problem in one persistent launch.
+ *   psi  host, packed parameters.  V, U: host arrays of n_problems DEVICE pointers, each
+ *   an n_b x R column-major block (leading dimension n_b); 1 <= R <= 32. */
+ulisse_status ulisse_batch_kmv(ulisse_ctx *ctx, const double *psi, const float *const *V, int R,
+                               float *const *U);
+
+/* Unbiased gradient estimates of every problem (as ulisse_grad, per problem).
+ *   psi, g  host, packed.   stats: NULL or n_problems x (1 + n_probes) entries. */
+ulisse_status ulisse_batch_grad(ulisse_ctx *ctx, const double *psi, unsigned long long step,
+                                double *g, ulisse_col_stats *stats);
+
+/* One SGLD step of every problem (as ulisse_sgld_step with M = I and a flat prior).
+ *   psi_inout host, packed; g_out NULL or host, packed. */
+ulisse_status ulisse_batch_sgld_step(ulisse_ctx *ctx, double *psi_inout, double eps_t,
+                                     unsigned long long step, double *g_out);
+
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);
 

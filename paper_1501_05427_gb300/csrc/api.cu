@@ -10,6 +10,7 @@
 #include "../../include/ulisse.h"
 #include "solver_kernels.cuh"
 #include "warm_start.cuh"
+#include "batch.cuh"
 
 using namespace ulisse;
 
@@ -77,6 +78,24 @@ struct ulisse_ctx {
   unsigned long long ws_seed = 0, ws_batches = 0;
   float* ws_c = nullptr;
   std::vector<void*> ws_allocs;
+
+  int meta_grad_R = -1;       // column count the gradient's column metadata was uploaded for
+
+  // batched context (ulisse_create_batched): one sub-context per problem
+  bool batched = false;
+  std::vector<ulisse_ctx*> subs;
+  std::vector<int> sub_p_off;      // offset of each problem's parameters in the packed vector
+  BatchItem* b_items = nullptr;
+  int b_n_items = 0;
+  BatchKmvDesc* b_kdesc = nullptr;
+  BatchGradDesc* b_gdesc = nullptr;
+  int* b_queue = nullptr;
+  int* b_nlive = nullptr;          // device, one live count per problem
+  int* b_h_nlive = nullptr;        // pinned
+  int* b_rcount = nullptr;         // device, column count of ulisse_batch_kmv per problem
+  int* b_h_status = nullptr;       // pinned, one status word per problem
+  double* b_gpart = nullptr;       // n_items x kMaxP
+  double* b_g = nullptr;           // problems x kMaxP
 
   // event timing of the O(n^2) kernels (ulisse_profile_enable)
   bool prof = false;
@@ -561,8 +580,11 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
   return ULISSE_OK;
 }
 
-// Whole gradient path for one step (a1..a6): psi must already be in psi_dev.
-static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step) {
+// Whole gradient path for one step (a1..a6): psi must already be in psi_dev.  With
+// prologue_only the call stops after the probes and the column metadata (a batch runs the
+// solves and the gradient pass of all its problems together).
+static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step,
+                               bool prologue_only = false) {
   const int nr = ctx->cfg.n_probes, R = 1 + nr;
   CKS(ensure_columns(ctx, R, R + 1));
   CKS(ensure_grad_maps(ctx, nr));
@@ -580,10 +602,15 @@ static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step) {
                                                        ctx->cfg.probe_kind, ctx->cfg.seed, epoch);
   CK(cudaGetLastError());
   ctx->launches++;
-  std::vector<int> n_est(R, 1);
-  n_est[0] = 2;
-  int tot = 0;
-  CKS(upload_meta(ctx, R, n_est.data(), &tot));
+  if (ctx->meta_grad_R != R) {
+    // column metadata (estimator counts, offsets, stream ids) survives the solves
+    std::vector<int> n_est(R, 1);
+    n_est[0] = 2;
+    int tot = 0;
+    CKS(upload_meta(ctx, R, n_est.data(), &tot));
+    ctx->meta_grad_R = R;
+  }
+  if (prologue_only) return ULISSE_OK;
   int s0_cols = 0;
   if (ctx->ws_use && ctx->ws_trained) {
     // learned warm start for the y column; the probe columns start from zero
@@ -764,6 +791,7 @@ static ulisse_status copy_stats(ulisse_ctx* ctx, ulisse_col_stats* stats, int R)
 static ulisse_status kmv_common(ulisse_ctx* ctx, const double* psi, int which, const void* V,
                                 int R, void* U, bool f64_data) {
   if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (!V || !U || R < 1 || R > 4096) return fail(ctx, ULISSE_ERR_ARG, "V/U null or R out of range");
   if (which < -1 || which > ctx->d + 1) return fail(ctx, ULISSE_ERR_ARG, "which out of range");
   if (f64_data && !ctx->f64)
@@ -812,6 +840,7 @@ ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, i
                            const int* n_est, const float* S0, float* S_est,
                            unsigned long long step, ulisse_col_stats* stats) {
   if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (!B || !S_est || R < 1 || R > 1024) return fail(ctx, ULISSE_ERR_ARG, "B/S_est null or R out of range");
   int tot = 0;
   if (n_est)
@@ -839,6 +868,7 @@ ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, i
   CKS(in_cols(B, ctx->B));
   if (S0) CKS(in_cols(S0, ctx->S));
   CKS(upload_meta(ctx, R, n_est, &tot));
+  ctx->meta_grad_R = -1;
   CKS(solve_dispatch(ctx, R, S0 ? R : 0, step));
   if (!ctx->f64) {
     CK(cudaMemcpy2DAsync(S_est, n * 4, ctx->SE, ctx->ldn * 4, n * 4, tot,
@@ -857,6 +887,7 @@ ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, i
 ulisse_status ulisse_grad(ulisse_ctx* ctx, const double* psi, unsigned long long step, double* g,
                           ulisse_col_stats* stats) {
   if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (!g) return fail(ctx, ULISSE_ERR_ARG, "g is null");
   CKS(set_psi_host(ctx, psi));
   CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
@@ -893,6 +924,7 @@ static ulisse_status upload_M_prior(ulisse_ctx* ctx, const double* M, const doub
 ulisse_status ulisse_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t, const double* M,
                                const double* prior_grad, unsigned long long step, double* g_out) {
   if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (!(eps_t >= 0.0) || !std::isfinite(eps_t)) return fail(ctx, ULISSE_ERR_ARG, "eps_t invalid");
   CKS(set_psi_host(ctx, psi_inout));
   const double *Md, *pd;
@@ -921,6 +953,7 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
                                 int n_steps, const double* M, const double* prior_grad,
                                 unsigned long long step0, double* trace_dev) {
   if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (!psi_dev || !eps_dev || n_steps < 0) return fail(ctx, ULISSE_ERR_ARG, "bad chain arguments");
   const int p = ctx->d + 2;
   const double *Md, *pd;
@@ -982,6 +1015,7 @@ static ulisse_status ws_alloc(ulisse_ctx* ctx, void** p, size_t bytes) {
 ulisse_status ulisse_ws_init(ulisse_ctx* ctx, const ulisse_ws_config* cfg) {
   if (!ctx) return ULISSE_ERR_ARG;
   if (!cfg) return fail(ctx, ULISSE_ERR_ARG, "cfg is null");
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   if (ctx->f64) return fail(ctx, ULISSE_ERR_ARG, "the warm start needs an FP32 or mixed context");
   if (ctx->ws_ready) return fail(ctx, ULISSE_ERR_ARG, "warm start already initialised");
   const int A = cfg->n_anchors, H = cfg->hidden, m = cfg->n_rows, P = cfg->max_pairs;
@@ -1224,12 +1258,361 @@ ulisse_status ulisse_ws_x0(ulisse_ctx* ctx, const double* psi, int bf16, float* 
   return ULISSE_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched contexts: many independent problems, O(n^2) passes in one persistent launch
+// ---------------------------------------------------------------------------------------
+#define BATCHED_ONLY(ctx)                                                                 \
+  do {                                                                                    \
+    if (!(ctx)) return ULISSE_ERR_ARG;                                                    \
+    if (!(ctx)->batched) return fail((ctx), ULISSE_ERR_ARG, "not a batched context");     \
+  } while (0)
+
+ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long long* n,
+                                    const int* d, const float* const* X, const float* const* y,
+                                    const ulisse_config* cfg, void* stream) {
+  if (!out) return fail(nullptr, ULISSE_ERR_ARG, "out is null");
+  *out = nullptr;
+  if (n_problems < 1 || n_problems > 4096 || !n || !d || !X || !y || !cfg)
+    return fail(nullptr, ULISSE_ERR_ARG, "bad batch description");
+  if (check_cfg(cfg) != ULISSE_OK) return fail(nullptr, ULISSE_ERR_ARG, "invalid config");
+  if (cfg->precision != ULISSE_PREC_FP32)
+    return fail(nullptr, ULISSE_ERR_ARG, "batched contexts run the FP32 path");
+  if (cfg->n_probes > 16) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take n_probes <= 16");
+  for (int b = 0; b < n_problems; ++b)
+    if (d[b] < 1 || d[b] > kBatchMaxDP) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take d <= 8");
+  ulisse_ctx* ctx = new ulisse_ctx();
+  ctx->stream = (cudaStream_t)stream;
+  ctx->cfg = *cfg;
+  ctx->batched = true;
+  auto bail = [&](ulisse_status s) {
+    g_create_error = ctx->err;
+    ulisse_destroy(ctx);
+    return s;
+  };
+  if (cudaGetDevice(&ctx->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device) !=
+          cudaSuccess) {
+    ctx->err = "no CUDA device";
+    return bail(ULISSE_ERR_CUDA);
+  }
+  int poff = 0;
+  for (int b = 0; b < n_problems; ++b) {
+    ulisse_config sc = *cfg;
+    sc.seed = cfg->seed + (unsigned long long)b;   // problem b draws from its own streams
+    ulisse_ctx* sub = nullptr;
+    const ulisse_status s = create_impl(&sub, X[b], y[b], n[b], d[b], &sc, stream,
+                                        cudaMemcpyDeviceToDevice);
+    if (s != ULISSE_OK) {
+      ctx->err = "problem " + std::to_string(b) + ": " + g_create_error;
+      return bail(s);
+    }
+    ctx->subs.push_back(sub);
+    ctx->sub_p_off.push_back(poff);
+    poff += d[b] + 2;
+    ctx->n += n[b];
+  }
+  // Work list: one item per (problem, 256-row block), longest rows first.
+  std::vector<BatchItem> items;
+  int slot = 0;
+  for (int b = 0; b < n_problems; ++b) {
+    const int nrb = (int)((n[b] + kBatchBM - 1) / kBatchBM);
+    for (int rb = 0; rb < nrb; ++rb) items.push_back(BatchItem{b, rb, slot + rb, 0});
+    slot += nrb;
+  }
+  std::stable_sort(items.begin(), items.end(), [&](const BatchItem& a, const BatchItem& c) {
+    return n[a.prob] > n[c.prob];
+  });
+  ctx->b_n_items = (int)items.size();
+  ulisse_status s;
+  if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_items), sizeof(BatchItem) * items.size())) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_kdesc), sizeof(BatchKmvDesc) * n_problems)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_gdesc), sizeof(BatchGradDesc) * n_problems)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_queue), sizeof(int))) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_nlive), sizeof(int) * n_problems)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_rcount), sizeof(int) * n_problems)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_gpart), sizeof(double) * kMaxP * items.size())) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_g), sizeof(double) * kMaxP * n_problems)) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))))
+    return bail(s);
+  if (cudaMallocHost(&ctx->b_h_nlive, sizeof(int) * n_problems) != cudaSuccess ||
+      cudaMallocHost(&ctx->b_h_status, sizeof(int) * (n_problems + 1)) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) {
+    ctx->err = "cudaMallocHost failed";
+    return bail(ULISSE_ERR_NOMEM);
+  }
+  if (cudaMemcpyAsync(ctx->b_items, items.data(), sizeof(BatchItem) * items.size(),
+                      cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+    ctx->err = "upload of the work list failed";
+    return bail(ULISSE_ERR_CUDA);
+  }
+  *out = ctx;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_batch_size(const ulisse_ctx* ctx, int* n_problems, int* n_params) {
+  if (!ctx || !ctx->batched || !n_problems) return ULISSE_ERR_ARG;
+  *n_problems = (int)ctx->subs.size();
+  if (n_params) {
+    int t = 0;
+    for (const ulisse_ctx* sub : ctx->subs) t += sub->d + 2;
+    *n_params = t;
+  }
+  return ULISSE_OK;
+}
+
+static ulisse_status batch_set_psi(ulisse_ctx* ctx, const double* psi) {
+  if (!psi) return fail(ctx, ULISSE_ERR_ARG, "psi is null");
+  for (size_t b = 0; b < ctx->subs.size(); ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    if (!finite_psi(psi + ctx->sub_p_off[b], sub->d + 2))
+      return fail(ctx, ULISSE_ERR_ARG, "psi of problem " + std::to_string(b) + " not finite");
+    if (set_psi_host(sub, psi + ctx->sub_p_off[b]) != ULISSE_OK) {
+      ctx->err = sub->err;
+      return ULISSE_ERR_CUDA;
+    }
+  }
+  return ULISSE_OK;
+}
+
+// Status words of the batch and of every problem, OR-ed (synchronises the stream).
+static ulisse_status batch_read_status(ulisse_ctx* ctx, int* status) {
+  const int B = (int)ctx->subs.size();
+  CK(cudaMemcpyAsync(ctx->b_h_status + B, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  for (int b = 0; b < B; ++b)
+    CK(cudaMemcpyAsync(ctx->b_h_status + b, ctx->subs[b]->status_dev, sizeof(int),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  int st = 0;
+  for (int b = 0; b <= B; ++b) st |= ctx->b_h_status[b];
+  *status = st;
+  return ULISSE_OK;
+}
+
+static ulisse_status batch_clear_status(ulisse_ctx* ctx) {
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  for (ulisse_ctx* sub : ctx->subs)
+    CK(cudaMemsetAsync(sub->status_dev, 0, sizeof(int), ctx->stream));
+  return ULISSE_OK;
+}
+
+// A sub-context's failure (its message) reported on the batch.
+#define SUBS(ctx, sub, expr)                  \
+  do {                                        \
+    ulisse_status s_ = (expr);                \
+    if (s_ != ULISSE_OK) {                    \
+      (ctx)->err = (sub)->err;                \
+      return s_;                              \
+    }                                         \
+  } while (0)
+
+ulisse_status ulisse_batch_kmv(ulisse_ctx* ctx, const double* psi, const float* const* V, int R,
+                               float* const* U) {
+  BATCHED_ONLY(ctx);
+  if (!V || !U || R < 1 || R > 32) return fail(ctx, ULISSE_ERR_ARG, "V/U null or R out of 1..32");
+  const int B = (int)ctx->subs.size();
+  for (int b = 0; b < B; ++b)
+    if (!V[b] || !U[b]) return fail(ctx, ULISSE_ERR_ARG, "V[b] or U[b] is null");
+  CKS(batch_set_psi(ctx, psi));
+  CKS(batch_clear_status(ctx));
+  std::vector<BatchKmvDesc> desc(B);
+  std::vector<int> rc(B, R);
+  double entries = 0.0;
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    SUBS(ctx, sub, prescale(sub));
+    SUBS(ctx, sub, ensure_columns(sub, R, R));
+    CK(cudaMemcpy2DAsync(sub->D, sub->ldn * 4, V[b], sub->n * 4, sub->n * 4, R,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    desc[b] = BatchKmvDesc{(const float*)sub->xhat, sub->n, sub->DP, 0, sub->params,
+                           (const float*)sub->D, sub->ldn, sub->iota, (float*)sub->KD, sub->ldn,
+                           sub->iota, ctx->b_rcount + b};
+    entries += (double)sub->n * (double)sub->n * R;
+  }
+  CK(cudaMemcpyAsync(ctx->b_kdesc, desc.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_rcount, rc.data(), sizeof(int) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue, R, ctx->num_sms,
+                      ctx->status_dev, ctx->stream));
+  ctx->launches++;
+  ctx->mvp_rounds++;
+  ctx->entry_rhs += entries;
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    CK(cudaMemcpy2DAsync(U[b], sub->n * 4, sub->KD, sub->ldn * 4, sub->n * 4, R,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  int st = 0;
+  CKS(batch_read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+// The gradient path of every problem for one step (psi already on each sub-context): per
+// problem the prologue (prescale, probes, metadata), CG + ULISSE in lock-step rounds with
+// one persistent K V launch per round over all live columns of all problems, then one
+// persistent gradient launch.  The gradients land in b_g (kMaxP doubles per problem).
+static ulisse_status batch_grad_core(ulisse_ctx* ctx, unsigned long long step) {
+  const int B = (int)ctx->subs.size();
+  const int nr = ctx->cfg.n_probes, R = 1 + nr;
+  std::vector<CgArgs<float>> args(B);
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    SUBS(ctx, sub, grad_core(sub, step, true));
+    args[b] = cg_args<float>(sub, 0, step);
+    cg_init_kernel<float><<<R, kCgNT, 0, ctx->stream>>>(args[b]);
+    CK(cudaGetLastError());
+  }
+  ctx->launches += B;
+  std::vector<BatchKmvDesc> kd(B);
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    kd[b] = BatchKmvDesc{(const float*)sub->xhat, sub->n, sub->DP, 0, sub->params,
+                         (const float*)sub->D, sub->ldn, sub->live, (float*)sub->KD, sub->ldn,
+                         sub->live, ctx->b_nlive + b};
+  }
+  CK(cudaMemcpyAsync(ctx->b_kdesc, kd.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  std::vector<int> n_prev(B, 0);
+  std::vector<char> active(B, 1);
+  for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
+    for (int b = 0; b < B; ++b) {
+      if (!active[b]) continue;
+      ulisse_ctx* sub = ctx->subs[b];
+      compact_kernel<<<1, 32, 0, ctx->stream>>>(sub->st, sub->st_next, R, n_prev[b], sub->live,
+                                                ctx->b_nlive + b);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(ctx->b_h_nlive, ctx->b_nlive, sizeof(int) * B, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    int rmax = 0, n_active = 0;
+    double entries = 0.0;
+    for (int b = 0; b < B; ++b) {
+      if (!active[b]) continue;
+      ++n_active;
+      const int nl = ctx->b_h_nlive[b];
+      rmax = std::max(rmax, nl);
+      entries += (double)ctx->subs[b]->n * (double)ctx->subs[b]->n * nl;
+    }
+    ctx->launches += n_active;
+    if (rmax == 0) break;
+    CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue, rmax,
+                        ctx->num_sms, ctx->status_dev, ctx->stream));
+    ctx->launches++;
+    ctx->mvp_rounds++;
+    ctx->entry_rhs += entries;
+    for (int b = 0; b < B; ++b) {
+      if (!active[b]) continue;
+      const int nl = ctx->b_h_nlive[b];
+      n_prev[b] = nl;
+      if (nl == 0) {
+        active[b] = 0;
+        continue;
+      }
+      ulisse_ctx* sub = ctx->subs[b];
+      CgArgs<float>& a = args[b];
+      // about two CTAs per SM over all of this problem's live columns, >= 2048 rows each
+      const long long target = std::max(1, (2 * ctx->num_sms + nl - 1) / nl);
+      long long ch = std::max<long long>((sub->n + target - 1) / target, 2048);
+      ch = std::max<long long>(ch, (sub->n + kMaxCgChunks - 1) / kMaxCgChunks);
+      ch = (ch + 255) / 256 * 256;
+      a.chunk = ch;
+      a.nchunk = (int)((sub->n + ch - 1) / ch);
+      const dim3 grid(a.nchunk, nl);
+      cg_dot_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+      cg_update_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+      cg_finish_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+      ctx->launches += 3;
+    }
+    CK(cudaGetLastError());
+  }
+  // a2 (second estimate of K^{-1} y) becomes the right factor of the quadratic term.
+  std::vector<BatchGradDesc> gd(B);
+  int slot0 = 0;
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    CK(cudaMemcpyAsync(sub->B, (char*)sub->SE + sub->ldn * 4, sub->ldn * 4,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    const int nslots = (int)((sub->n + kBatchBM - 1) / kBatchBM);
+    gd[b] = BatchGradDesc{(const float*)sub->xhat, sub->n, sub->DP, sub->d, sub->params,
+                          (const float*)sub->SE, sub->amap, (const float*)sub->sa_dev,
+                          (const float*)sub->B, sub->bmap, sub->ldn, R, slot0, nslots, 0,
+                          ctx->b_g + (long long)b * kMaxP};
+    slot0 += nslots;
+    ctx->entry_rhs += (double)sub->n * (double)sub->n * R;
+  }
+  CK(cudaMemcpyAsync(ctx->b_gdesc, gd.data(), sizeof(BatchGradDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(launch_grad_batch(ctx->b_gdesc, B, ctx->b_items, ctx->b_n_items, ctx->b_queue, ctx->b_gpart,
+                       R, ctx->num_sms, ctx->status_dev, ctx->stream));
+  ctx->launches += 2;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_batch_grad(ulisse_ctx* ctx, const double* psi, unsigned long long step,
+                                double* g, ulisse_col_stats* stats) {
+  BATCHED_ONLY(ctx);
+  if (!g) return fail(ctx, ULISSE_ERR_ARG, "g is null");
+  CKS(batch_set_psi(ctx, psi));
+  CKS(batch_clear_status(ctx));
+  CKS(batch_grad_core(ctx, step));
+  const int B = (int)ctx->subs.size();
+  std::vector<double> gall((size_t)B * kMaxP);
+  CK(cudaMemcpyAsync(gall.data(), ctx->b_g, sizeof(double) * gall.size(), cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  int st = 0;
+  CKS(batch_read_status(ctx, &st));
+  for (int b = 0; b < B; ++b)
+    for (int k = 0; k < ctx->subs[b]->d + 2; ++k) g[ctx->sub_p_off[b] + k] = gall[(size_t)b * kMaxP + k];
+  if (stats) {
+    const int R = 1 + ctx->cfg.n_probes;
+    for (int b = 0; b < B; ++b) SUBS(ctx, ctx->subs[b], copy_stats(ctx->subs[b], stats + (size_t)b * R, R));
+  }
+  return status_to_result(ctx, st);
+}
+
+ulisse_status ulisse_batch_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t,
+                                     unsigned long long step, double* g_out) {
+  BATCHED_ONLY(ctx);
+  if (!(eps_t >= 0.0) || !std::isfinite(eps_t)) return fail(ctx, ULISSE_ERR_ARG, "eps_t invalid");
+  CKS(batch_set_psi(ctx, psi_inout));
+  CKS(batch_clear_status(ctx));
+  CKS(batch_grad_core(ctx, step));
+  const int B = (int)ctx->subs.size();
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    sgld_kernel<<<1, 32, 0, ctx->stream>>>(sub->psi_dev, ctx->b_g + (long long)b * kMaxP, nullptr,
+                                           nullptr, nullptr, eps_t, sub->d + 2, sub->cfg.seed,
+                                           step, nullptr, sub->status_dev);
+  }
+  CK(cudaGetLastError());
+  ctx->launches += B;
+  int st = 0;
+  CKS(batch_read_status(ctx, &st));
+  ulisse_status r = status_to_result(ctx, st);
+  if (r == ULISSE_ERR_ARG) return r;
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    CK(cudaMemcpyAsync(psi_inout + ctx->sub_p_off[b], sub->psi_dev, sizeof(double) * (sub->d + 2),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_out)
+      CK(cudaMemcpyAsync(g_out + ctx->sub_p_off[b], ctx->b_g + (long long)b * kMaxP,
+                         sizeof(double) * (sub->d + 2), cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return r;
+}
+
 ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,
                               long long* kernel_launches) {
   if (!ctx) return ULISSE_ERR_ARG;
+  long long launches = ctx->launches;
+  for (const ulisse_ctx* sub : ctx->subs) launches += sub->launches;   // batched problems
   if (mvp_rounds) *mvp_rounds = ctx->mvp_rounds;
   if (entry_rhs) *entry_rhs = ctx->entry_rhs;
-  if (kernel_launches) *kernel_launches = ctx->launches;
+  if (kernel_launches) *kernel_launches = launches;
   return ULISSE_OK;
 }
 
@@ -1276,6 +1659,15 @@ void ulisse_destroy(ulisse_ctx* ctx) {
     dev_free(*p);
   for (void* p : ctx->ws_allocs) cudaFree(p);
   ctx->ws_allocs.clear();
+  for (ulisse_ctx* sub : ctx->subs) ulisse_destroy(sub);
+  ctx->subs.clear();
+  for (void** p : {reinterpret_cast<void**>(&ctx->b_items), reinterpret_cast<void**>(&ctx->b_kdesc),
+                   reinterpret_cast<void**>(&ctx->b_gdesc), reinterpret_cast<void**>(&ctx->b_queue),
+                   reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),
+                   reinterpret_cast<void**>(&ctx->b_gpart), reinterpret_cast<void**>(&ctx->b_g)})
+    dev_free(*p);
+  if (ctx->b_h_nlive) cudaFreeHost(ctx->b_h_nlive);
+  if (ctx->b_h_status) cudaFreeHost(ctx->b_h_status);
   prof_drain(ctx);
   for (auto& e : ctx->free_events) {
     cudaEventDestroy(e.first);

@@ -32,7 +32,8 @@ EXPORTED = [
     "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
     "ulisse_counters", "ulisse_profile_enable", "ulisse_profile_read", "ulisse_last_error",
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
-    "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0",
+    "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
+    "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
 ]
 
 
@@ -119,6 +120,11 @@ def load():
     lib.ulisse_ws_loss_grad.argtypes = [P, ctypes.POINTER(D), P]
     lib.ulisse_ws_export.argtypes = [P, ctypes.POINTER(ulisse_ws_state)]
     lib.ulisse_ws_x0.argtypes = [P, P, I, P]
+    lib.ulisse_create_batched.argtypes = [PP, I, P, P, P, P, cfgp, P]
+    lib.ulisse_batch_size.argtypes = [P, ctypes.POINTER(I), ctypes.POINTER(I)]
+    lib.ulisse_batch_kmv.argtypes = [P, P, P, I, P]
+    lib.ulisse_batch_grad.argtypes = [P, P, U64, P, sp]
+    lib.ulisse_batch_sgld_step.argtypes = [P, P, D, U64, P]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -383,6 +389,85 @@ def ulisse_profile_read(ctx: Context, reset=False):
     return ctx.profile_read(reset)
 
 
+class BatchContext:
+    """Many independent GP problems advanced together (ulisse_create_batched).
+
+    Parameters and gradients are packed: problem b's d_b + 2 values follow problem b-1's.
+    Problem b draws from the random streams of seed cfg.seed + b."""
+
+    def __init__(self, Xs, ys, cfg: ulisse_config | None = None, stream=None):
+        import torch
+        self._lib = load()
+        cfg = cfg or ulisse_config_default()
+        self.cfg = cfg
+        self._keep = [(X.contiguous().float(), y.contiguous().float()) for X, y in zip(Xs, ys)]
+        B = len(self._keep)
+        self.ns = [int(X.shape[0]) for X, _ in self._keep]
+        self.ds = [int(X.shape[1]) for X, _ in self._keep]
+        self.ps = [d + 2 for d in self.ds]
+        self.p_off = np.concatenate([[0], np.cumsum(self.ps)[:-1]]).astype(int)
+        self.n_params = int(sum(self.ps))
+        n_arr = np.array(self.ns, dtype=np.int64)
+        d_arr = np.array(self.ds, dtype=np.int32)
+        xp = (ctypes.c_void_p * B)(*[X.data_ptr() for X, _ in self._keep])
+        yp = (ctypes.c_void_p * B)(*[y.data_ptr() for _, y in self._keep])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        st = self._lib.ulisse_create_batched(ctypes.byref(h), B, _hptr(n_arr), _hptr(d_arr),
+                                             ctypes.cast(xp, ctypes.c_void_p),
+                                             ctypes.cast(yp, ctypes.c_void_p), ctypes.byref(cfg),
+                                             ctypes.c_void_p(self.stream.cuda_stream))
+        if st != ULISSE_OK:
+            raise UlisseError(st, self._lib.ulisse_last_error(None).decode())
+        self._h = h
+        self.n_problems = B
+
+    _check = Context._check
+    close = Context.close
+    __del__ = Context.__del__
+    __enter__ = Context.__enter__
+    __exit__ = Context.__exit__
+
+    def split(self, packed):
+        """Packed vector -> list of per-problem arrays."""
+        return [np.asarray(packed)[o:o + p] for o, p in zip(self.p_off, self.ps)]
+
+    def kmv(self, psi, Vs):
+        """U_b = K_b V_b for all problems.  Vs: list of (n_b, R) CUDA tensors (same R)."""
+        import torch
+        Vc = [_colmajor(V.float()) for V in Vs]
+        R = Vc[0].shape[1]
+        Us = [torch.empty((R, n), dtype=torch.float32, device=V.device).t()
+              for V, n in zip(Vc, self.ns)]
+        vp = (ctypes.c_void_p * self.n_problems)(*[V.data_ptr() for V in Vc])
+        up = (ctypes.c_void_p * self.n_problems)(*[U.data_ptr() for U in Us])
+        psi = _f64_host(psi, self.n_params)
+        self._check(self._lib.ulisse_batch_kmv(self._h, _hptr(psi), ctypes.cast(vp, ctypes.c_void_p),
+                                               R, ctypes.cast(up, ctypes.c_void_p)))
+        return Us
+
+    def grad(self, psi, step=0, allow=()):
+        """Packed gradient estimates (host numpy) and per-problem column stats."""
+        psi = _f64_host(psi, self.n_params)
+        g = np.zeros(self.n_params)
+        R = 1 + self.cfg.n_probes
+        stats = (ulisse_col_stats * (R * self.n_problems))()
+        self._check(self._lib.ulisse_batch_grad(self._h, _hptr(psi), step, _hptr(g), stats), allow)
+        st = [(s.l, s.iterations, s.outcome, s.J0, s.J1) for s in stats]
+        return g, [st[b * R:(b + 1) * R] for b in range(self.n_problems)]
+
+    def sgld_step(self, psi, eps_t, step, allow=()):
+        """One SGLD step of every problem; returns (psi_new, g), packed."""
+        psi = np.array(psi, dtype=np.float64, copy=True)
+        assert psi.size == self.n_params
+        g = np.zeros(self.n_params)
+        self._check(self._lib.ulisse_batch_sgld_step(self._h, _hptr(psi), eps_t, step, _hptr(g)),
+                    allow)
+        return psi, g
+
+    counters = Context.counters
+
+
 def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
     """U = K V (or dK/dpsi_which V) through the allocation-free entry point: X (n, d) and
     V (n, R <= 32) CUDA float tensors; the library allocates nothing for this call."""
@@ -431,3 +516,26 @@ def ulisse_ws_x0(ctx: Context, psi, bf16=False):
 
 def ulisse_destroy(ctx: Context):
     ctx.close()
+
+
+def ulisse_create_batched(Xs, ys, cfg: ulisse_config | None = None, stream=None) -> BatchContext:
+    return BatchContext(Xs, ys, cfg, stream)
+
+
+def ulisse_batch_size(ctx: BatchContext):
+    n = ctypes.c_int()
+    p = ctypes.c_int()
+    ctx._check(ctx._lib.ulisse_batch_size(ctx._h, ctypes.byref(n), ctypes.byref(p)))
+    return n.value, p.value
+
+
+def ulisse_batch_kmv(ctx: BatchContext, psi, Vs):
+    return ctx.kmv(psi, Vs)
+
+
+def ulisse_batch_grad(ctx: BatchContext, psi, step=0):
+    return ctx.grad(psi, step)
+
+
+def ulisse_batch_sgld_step(ctx: BatchContext, psi, eps_t, step):
+    return ctx.sgld_step(psi, eps_t, step)
