@@ -357,6 +357,17 @@ ulisse_status ulisse_batch_grad(ulisse_ctx *ctx, const double *psi, unsigned lon
 ulisse_status ulisse_batch_sgld_step(ulisse_ctx *ctx, double *psi_inout, double eps_t,
                                      unsigned long long step, double *g_out);
 
+/* ulisse_sgld_chain runs each step as ONE launch of a CUDA graph (enable != 0, the default)
+ * or from the host loop (0).  The graph holds the whole step: prescale, probes, the CG +
+ * ULISSE loop as a conditional WHILE node (its body compacts the live columns on the device
+ * and a SWITCH node picks the branch compiled for that many live columns), the fused
+ * gradient and the update; the step number, step size and trace slot are read from the
+ * device.  Both forms launch the same kernels with the same arguments and give the same
+ * results.  The chain uses the host loop while the event timing (ulisse_profile_enable) is
+ * on or warm-start pairs are recorded.  The graph is captured on first use and again after
+ * a call that reallocated the context's buffers. */
+ulisse_status ulisse_set_graph(ulisse_ctx *ctx, int enable);
+
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);
 

@@ -81,6 +81,20 @@ struct ulisse_ctx {
 
   int meta_grad_R = -1;       // column count the gradient's column metadata was uploaded for
 
+  // CUDA graph of one SGLD step (ulisse_sgld_chain)
+  bool planning = false;      // launch helpers only size their scratch
+  bool capturing = false;     // launch helpers are being captured: no host-side counting
+  bool graph_enabled = true;
+  cudaStream_t cap_stream = nullptr, cap_stream2 = nullptr;
+  cudaGraph_t step_graph = nullptr;
+  cudaGraphExec_t step_exec = nullptr;
+  long long graph_key = -1;   // configuration the graph was captured for
+  ChainSlot* chain = nullptr; // device
+  long long* gstat = nullptr; // device: rounds, sum of live columns, launches, rounds this step
+  long long graph_launches_fixed = 0;  // kernel launches per step outside the CG loop
+  double graph_entries_fixed = 0.0;    // entries x right-hand sides per step outside the loop
+  long long graph_rounds_fixed = 0;
+
   // batched context (ulisse_create_batched): one sub-context per problem
   bool batched = false;
   std::vector<ulisse_ctx*> subs;
@@ -192,6 +206,7 @@ static void dev_free(void*& p) {
 // Column buffers for at least R solver columns and R_est estimate columns.
 static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
   if (R <= ctx->cap && R_est <= ctx->cap_est) return ULISSE_OK;
+  ctx->graph_key = -1;   // a captured step graph holds the old buffers
   const int cap = std::max(R, ctx->cap), cap_est = std::max(R_est, ctx->cap_est);
   CK(cudaStreamSynchronize(ctx->stream));
   for (void** p : {&ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD, &ctx->SE}) dev_free(*p);
@@ -246,16 +261,37 @@ static ulisse_status prescale(ulisse_ctx* ctx) {
     prescale_kernel<float><<<blocks, 256, 0, ctx->stream>>>(
         ctx->psi_dev, ctx->X, (float*)ctx->xhat, ctx->n, ctx->d, ctx->DP, ctx->params);
   CK(cudaGetLastError());
-  ctx->launches++;
+  if (!ctx->capturing) ctx->launches++;
   if (ctx->mixed) {
     CK(launch_prescale_tc((const float*)ctx->xhat, ctx->DP, ctx->d, ctx->n, ctx->ld128,
                           ctx->bneg, ctx->num_sms, ctx->stream));
-    ctx->launches++;
+    if (!ctx->capturing) ctx->launches++;
   }
   return ULISSE_OK;
 }
 
 // U[:, umap[r]] = A V[:, vmap[r]] for r < R (chunks of kMaxRChunk columns per launch).
+// Grow the split-j scratch of the K V kernels to at least the given sizes.
+static ulisse_status grow_kmv_scratch(ulisse_ctx* ctx, size_t need_bytes, int need_counters) {
+  if (need_bytes <= ctx->partials_bytes && need_counters <= ctx->counters_len) return ULISSE_OK;
+  ctx->graph_key = -1;
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (need_bytes > ctx->partials_bytes) {
+    dev_free(ctx->partials);
+    ctx->partials_bytes = 0;
+    CKS(dev_alloc(ctx, &ctx->partials, need_bytes));
+    ctx->partials_bytes = need_bytes;
+  }
+  if (need_counters > ctx->counters_len) {
+    dev_free(reinterpret_cast<void*&>(ctx->counters));
+    ctx->counters_len = 0;
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->counters), sizeof(int) * need_counters));
+    ctx->counters_len = need_counters;
+  }
+  return ULISSE_OK;
+}
+
+// U[:, umap[r]] = A V[:, vmap[r]] for r < R (chunks of 64 columns per launch).
 static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap, int R, void* U,
                                 const int* umap) {
   for (int c0 = 0; c0 < R; c0 += 64) {
@@ -276,6 +312,14 @@ static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap,
     L.params = ctx->params;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
+    if (ctx->planning) {
+      L.plan_only = true;
+      cudaError_t e = launch_kmv_tc(L, ctx->stream);
+      if (e != cudaSuccess)
+        return fail(ctx, ULISSE_ERR_CUDA, std::string("tensor-core K V plan: ") + cudaGetErrorString(e));
+      CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
+      continue;
+    }
     for (int attempt = 0; attempt < 2; ++attempt) {
       L.partials = ctx->partials;
       L.partials_bytes = ctx->partials_bytes;
@@ -291,28 +335,15 @@ static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap,
           ctx->free_events.push_back({ea, eb});
       }
       if (e == cudaSuccess) {
-        ctx->launches += 2;
+        if (!ctx->capturing) ctx->launches += 2;
         break;
       }
-      if (e != cudaErrorMemoryAllocation || attempt == 1)
+      if (e != cudaErrorMemoryAllocation || attempt == 1 || ctx->capturing)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("tensor-core K V launch: ") + cudaGetErrorString(e));
       cudaGetLastError();
-      CK(cudaStreamSynchronize(ctx->stream));
-      if (L.need_partials_bytes > ctx->partials_bytes) {
-        dev_free(ctx->partials);
-        ctx->partials_bytes = 0;
-        CKS(dev_alloc(ctx, &ctx->partials, L.need_partials_bytes));
-        ctx->partials_bytes = L.need_partials_bytes;
-      }
-      if (L.need_counters > ctx->counters_len) {
-        dev_free(reinterpret_cast<void*&>(ctx->counters));
-        ctx->counters_len = 0;
-        CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->counters),
-                      sizeof(int) * L.need_counters));
-        ctx->counters_len = L.need_counters;
-      }
+      CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
     }
-    ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
+    if (!ctx->capturing) ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
   }
   return ULISSE_OK;
 }
@@ -340,6 +371,14 @@ static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, in
     L.tm = ctx->cfg.kmv_rows_per_thread;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
+    if (ctx->planning) {
+      L.plan_only = true;
+      cudaError_t e = ctx->f64 ? launch_kmv_f64(L, ctx->stream) : launch_kmv_f32(L, ctx->stream);
+      if (e != cudaSuccess)
+        return fail(ctx, ULISSE_ERR_CUDA, std::string("K V plan: ") + cudaGetErrorString(e));
+      CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
+      continue;
+    }
     for (int attempt = 0; attempt < 2; ++attempt) {
       L.partials = ctx->partials;
       L.partials_bytes = ctx->partials_bytes;
@@ -356,29 +395,16 @@ static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, in
           ctx->free_events.push_back({ea, eb});
       }
       if (e == cudaSuccess) {
-        ctx->launches++;
+        if (!ctx->capturing) ctx->launches++;
         break;
       }
-      if (e != cudaErrorMemoryAllocation || attempt == 1)
+      if (e != cudaErrorMemoryAllocation || attempt == 1 || ctx->capturing)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("K V launch: ") + cudaGetErrorString(e));
       cudaGetLastError();
       // Grow the split-j scratch to what this launch needs, then retry.
-      CK(cudaStreamSynchronize(ctx->stream));
-      if (L.need_partials_bytes > ctx->partials_bytes) {
-        dev_free(ctx->partials);
-        ctx->partials_bytes = 0;
-        CKS(dev_alloc(ctx, &ctx->partials, L.need_partials_bytes));
-        ctx->partials_bytes = L.need_partials_bytes;
-      }
-      if (L.need_counters > ctx->counters_len) {
-        dev_free(reinterpret_cast<void*&>(ctx->counters));
-        ctx->counters_len = 0;
-        CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->counters),
-                      sizeof(int) * L.need_counters));
-        ctx->counters_len = L.need_counters;
-      }
+      CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
     }
-    ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
+    if (!ctx->capturing) ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)L.R;
   }
   return ULISSE_OK;
 }
@@ -426,6 +452,7 @@ static CgArgs<T> cg_args(ulisse_ctx* ctx, int has_s0, unsigned long long step) {
   a.has_s0 = has_s0;
   a.seed = ctx->cfg.seed;
   a.step = step;
+  a.cs = nullptr;
   a.status = ctx->status_dev;
   return a;
 }
@@ -554,29 +581,34 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
   for (int attempt = 0; attempt < 2; ++attempt) {
     L.partials = ctx->gpart;
     L.partials_len = ctx->gpart_len;
+    L.plan_only = ctx->planning;
     cudaEvent_t ea = nullptr, eb = nullptr;
     prof_begin(ctx, &ea, &eb);
     cudaError_t e = ctx->f64 ? launch_grad_f64(L, ctx->stream) : launch_grad_f32(L, ctx->stream);
     if (ctx->prof) {
-      if (e == cudaSuccess)
+      if (e == cudaSuccess && !ctx->planning)
         prof_end(ctx, 1, ea, eb, (double)ctx->n * ctx->n * (5.0 * ctx->d + 4.0 + 2.0 * M));
       else
         ctx->free_events.push_back({ea, eb});
     }
-    if (e == cudaSuccess) {
-      ctx->launches++;
+    if (e == cudaSuccess && !ctx->planning) {
+      if (!ctx->capturing) ctx->launches++;
       break;
     }
-    if (e != cudaErrorMemoryAllocation || attempt == 1)
+    if (e != cudaSuccess && (e != cudaErrorMemoryAllocation || attempt == 1 || ctx->capturing))
       return fail(ctx, ULISSE_ERR_CUDA, std::string("gradient launch: ") + cudaGetErrorString(e));
     cudaGetLastError();
-    CK(cudaStreamSynchronize(ctx->stream));
-    dev_free(reinterpret_cast<void*&>(ctx->gpart));
-    ctx->gpart_len = 0;
-    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gpart), sizeof(double) * L.need_partials_len));
-    ctx->gpart_len = L.need_partials_len;
+    if (L.need_partials_len > ctx->gpart_len) {
+      ctx->graph_key = -1;
+      CK(cudaStreamSynchronize(ctx->stream));
+      dev_free(reinterpret_cast<void*&>(ctx->gpart));
+      ctx->gpart_len = 0;
+      CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gpart), sizeof(double) * L.need_partials_len));
+      ctx->gpart_len = L.need_partials_len;
+    }
+    if (ctx->planning) return ULISSE_OK;
   }
-  ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)M;
+  if (!ctx->capturing) ctx->entry_rhs += (double)ctx->n * (double)ctx->n * (double)M;
   return ULISSE_OK;
 }
 
@@ -949,6 +981,210 @@ ulisse_status ulisse_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t,
   return r;
 }
 
+// ---------------------------------------------------------------------------------------
+// One SGLD step as a CUDA graph (ulisse_sgld_chain).  The data-dependent CG loop becomes a
+// WHILE node whose body is the compaction kernel and a SWITCH node with one branch per live
+// column count: branch k holds exactly the launches the host loop makes for k + 1 live
+// columns (same instantiations, same splits), so a graph step and a host-loop step give the
+// same results.  The step number, step size and trace slot come from a device chain slot.
+// ---------------------------------------------------------------------------------------
+static void graph_release(ulisse_ctx* ctx) {
+  if (ctx->step_exec) cudaGraphExecDestroy(ctx->step_exec);
+  if (ctx->step_graph) cudaGraphDestroy(ctx->step_graph);
+  ctx->step_exec = nullptr;
+  ctx->step_graph = nullptr;
+  ctx->graph_key = -1;
+}
+
+extern "C++" {
+template <typename T>
+static void cg_round_launches(ulisse_ctx* ctx, CgArgs<T>& a, int nl) {
+  const long long target = std::max(1, (2 * ctx->num_sms + nl - 1) / nl);
+  long long ch = std::max<long long>((ctx->n + target - 1) / target, 2048);
+  ch = std::max<long long>(ch, (ctx->n + kMaxCgChunks - 1) / kMaxCgChunks);
+  ch = (ch + 255) / 256 * 256;
+  a.chunk = ch;
+  a.nchunk = (int)((ctx->n + ch - 1) / ch);
+  const dim3 grid(a.nchunk, nl);
+  cg_dot_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+  cg_update_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+  cg_finish_kernel<T><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
+}
+
+template <typename T>
+static ulisse_status graph_capture_body(ulisse_ctx* ctx, int s0_cols) {
+  const int nr = ctx->cfg.n_probes, R = 1 + nr, p = ctx->d + 2;
+  CKS(prescale(ctx));
+  CK(cudaMemcpyAsync(ctx->B, ctx->y, ctx->ldn * ctx->esz, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  dim3 pg((unsigned)std::min<long long>((ctx->n + 255) / 256, 2LL * ctx->num_sms), nr);
+  probes_kernel<T><<<pg, 256, 0, ctx->stream>>>((T*)ctx->B, ctx->ldn, ctx->n, nr,
+                                                ctx->cfg.probe_kind, ctx->cfg.seed, 0,
+                                                ctx->chain, ctx->cfg.probe_refresh);
+  CK(cudaGetLastError());
+  if (s0_cols > 0) {
+    ws_x0(ctx->wsb, ctx->psi_dev, true, (const float*)ctx->xhat, ctx->DP, ctx->n, ctx->params,
+          ctx->ws_c, (float*)ctx->S, ctx->num_sms, ctx->stream);
+    CK(cudaGetLastError());
+    CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0,
+                       (size_t)(R - 1) * ctx->ldn * ctx->esz, ctx->stream));
+    CK(cudaMemsetAsync((char*)ctx->KD + (size_t)s0_cols * ctx->ldn * ctx->esz, 0,
+                       (size_t)(R - s0_cols) * ctx->ldn * ctx->esz, ctx->stream));
+    CKS(run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1));
+  }
+  CgArgs<T> a = cg_args<T>(ctx, s0_cols > 0, 0);
+  a.cs = ctx->chain;
+  cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->n_live_dev, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->gstat + 3, 0, sizeof(long long), ctx->stream));
+
+  // WHILE node on the outer graph
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  CK(cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+  cudaGraphConditionalHandle h_loop, h_branch;
+  CK(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams wp = {};
+  wp.type = cudaGraphNodeTypeConditional;
+  wp.conditional.handle = h_loop;
+  wp.conditional.type = cudaGraphCondTypeWhile;
+  wp.conditional.size = 1;
+  cudaGraphNode_t wnode;
+  CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &wp));
+  CK(cudaStreamUpdateCaptureDependencies(ctx->stream, &wnode, nullptr, 1,
+                                         cudaStreamSetCaptureDependencies));
+  cudaGraph_t body = wp.conditional.phGraph_out[0];
+
+  // loop body: compaction, then the SWITCH over the live column count
+  CK(cudaGraphConditionalHandleCreate(&h_branch, body, (unsigned)R, cudaGraphCondAssignDefault));
+  cudaStream_t outer = ctx->stream;
+  CK(cudaStreamBeginCaptureToGraph(ctx->cap_stream2, body, nullptr, nullptr, 0,
+                                   cudaStreamCaptureModeThreadLocal));
+  const int chunk_cols = ctx->mixed ? 64 : kMaxRChunk;
+  const int per_chunk = ctx->mixed ? 2 : 1;
+  compact_graph_kernel<<<1, 32, 0, ctx->cap_stream2>>>(
+      ctx->st, ctx->st_next, R, ctx->live, ctx->n_live_dev, h_loop, h_branch, chunk_cols,
+      per_chunk, 3, ctx->cfg.max_iter + 2, ctx->gstat, ctx->status_dev);
+  cudaError_t e = cudaGetLastError();
+  const cudaGraphNode_t* bdeps = nullptr;
+  size_t nbdeps = 0;
+  cudaGraph_t bg = nullptr;
+  if (e == cudaSuccess)
+    e = cudaStreamGetCaptureInfo(ctx->cap_stream2, &cst, nullptr, &bg, &bdeps, nullptr, &nbdeps);
+  cudaGraphNodeParams sp = {};
+  sp.type = cudaGraphNodeTypeConditional;
+  sp.conditional.handle = h_branch;
+  sp.conditional.type = cudaGraphCondTypeSwitch;
+  sp.conditional.size = (unsigned)R;
+  cudaGraphNode_t snode;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&snode, bg, bdeps, nullptr, nbdeps, &sp);
+  if (e == cudaSuccess)
+    e = cudaStreamUpdateCaptureDependencies(ctx->cap_stream2, &snode, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+  cudaGraph_t tmp = nullptr;
+  const cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream2, &tmp);
+  CK(e);
+  CK(e2);
+  // branch k: one CG round with k + 1 live columns
+  for (int k = 0; k < R; ++k) {
+    CK(cudaStreamBeginCaptureToGraph(ctx->cap_stream2, sp.conditional.phGraph_out[k], nullptr,
+                                     nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->cap_stream2;
+    ulisse_status r = run_kmv(ctx, ctx->D, ctx->live, k + 1, ctx->KD, ctx->live, kModeK, -1);
+    if (r == ULISSE_OK) cg_round_launches<T>(ctx, a, k + 1);
+    ctx->stream = outer;
+    const cudaError_t e3 = cudaGetLastError();
+    const cudaError_t e4 = cudaStreamEndCapture(ctx->cap_stream2, &tmp);
+    CKS(r);
+    CK(e3);
+    CK(e4);
+  }
+  // after the loop: the second estimate of K^{-1} y as the right factor, gradient, update
+  CK(cudaMemcpyAsync(ctx->B, (char*)ctx->SE + ctx->ldn * ctx->esz, ctx->ldn * ctx->esz,
+                     cudaMemcpyDeviceToDevice, ctx->stream));
+  CKS(run_grad(ctx, R));
+  sgld_chain_kernel<<<1, 32, 0, ctx->stream>>>(ctx->psi_dev, ctx->g_dev, ctx->M_dev,
+                                               ctx->prior_dev, p, ctx->cfg.seed, ctx->chain,
+                                               ctx->status_dev);
+  CK(cudaGetLastError());
+  return ULISSE_OK;
+}
+
+}  // extern "C++"
+
+static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
+  graph_release(ctx);
+  const int nr = ctx->cfg.n_probes, R = 1 + nr;
+  CKS(ensure_columns(ctx, R, R + 1));
+  CKS(ensure_grad_maps(ctx, nr));
+  if (ctx->meta_grad_R != R) {
+    std::vector<int> n_est(R, 1);
+    n_est[0] = 2;
+    int tot = 0;
+    CKS(upload_meta(ctx, R, n_est.data(), &tot));
+    ctx->meta_grad_R = R;
+  }
+  if (!ctx->cap_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+  }
+  // size every launch's scratch first: nothing may allocate inside the capture
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  ctx->planning = true;
+  ulisse_status r = ULISSE_OK;
+  for (int k = 1; k <= R && r == ULISSE_OK; ++k)
+    r = run_kmv(ctx, ctx->D, ctx->live, k, ctx->KD, ctx->live, kModeK, -1);
+  if (r == ULISSE_OK && s0_cols > 0)
+    r = run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1);
+  if (r == ULISSE_OK) r = run_grad(ctx, R);
+  ctx->planning = false;
+  if (r != ULISSE_OK) {
+    ctx->prof = prof;
+    return r;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaStream_t saved = ctx->stream;
+  ctx->stream = ctx->cap_stream;
+  ctx->capturing = true;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) r = ctx->f64 ? graph_capture_body<double>(ctx, s0_cols)
+                                     : graph_capture_body<float>(ctx, s0_cols);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+  ctx->stream = saved;
+  ctx->capturing = false;
+  ctx->prof = prof;
+  if (r != ULISSE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(ctx, ULISSE_ERR_CUDA, std::string("step graph capture: ") + cudaGetErrorString(e2));
+  }
+  ctx->step_graph = graph;
+  CK(cudaGraphInstantiate(&ctx->step_exec, graph, 0));
+  // what one launch does outside the CG loop (the loop's share is counted on the device)
+  const long long kmv_per = ctx->mixed ? 2 : 1, kmv_cols = ctx->mixed ? 64 : kMaxRChunk;
+  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + 1 + 1 +
+      (s0_cols > 0 ? 2 + kmv_per * ((s0_cols + kmv_cols - 1) / kmv_cols) : 0);
+  ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + s0_cols);
+  ctx->graph_rounds_fixed = s0_cols > 0 ? 1 : 0;
+  ctx->graph_key = s0_cols;
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_set_graph(ulisse_ctx* ctx, int enable) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
+  ctx->graph_enabled = enable != 0;
+  return ULISSE_OK;
+}
+
 ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* eps_dev,
                                 int n_steps, const double* M, const double* prior_grad,
                                 unsigned long long step0, double* trace_dev) {
@@ -961,6 +1197,37 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
   CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
   CK(cudaMemcpyAsync(ctx->psi_dev, psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
                      ctx->stream));
+  // Each step as one launch of the step graph, unless the event timing is on (it times
+  // single launches) or warm-start pairs are being recorded (host-side bookkeeping).
+  if (ctx->graph_enabled && !ctx->prof && !ctx->ws_record && n_steps > 0) {
+    if (!M) {
+      std::vector<double> I((size_t)p * p, 0.0);
+      for (int i = 0; i < p; ++i) I[(size_t)i * p + i] = 1.0;
+      CK(cudaMemcpyAsync(ctx->M_dev, I.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                         ctx->stream));
+    }
+    if (!prior_grad) CK(cudaMemsetAsync(ctx->prior_dev, 0, sizeof(double) * p, ctx->stream));
+    if (!ctx->chain) {
+      CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->chain), sizeof(ChainSlot)));
+      CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gstat), sizeof(long long) * 4));
+    }
+    const ChainSlot cs{0, step0, eps_dev, trace_dev};
+    CK(cudaMemcpyAsync(ctx->chain, &cs, sizeof(ChainSlot), cudaMemcpyHostToDevice, ctx->stream));
+    const int s0 = (ctx->ws_use && ctx->ws_trained) ? 1 : 0;
+    if (ctx->graph_key != s0) CKS(graph_build(ctx, s0));
+    for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
+    CK(cudaMemcpyAsync(psi_dev, ctx->psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
+                       ctx->stream));
+    long long gs[4] = {0, 0, 0, 0};
+    CK(cudaMemcpyAsync(gs, ctx->gstat, sizeof(gs), cudaMemcpyDeviceToHost, ctx->stream));
+    int st = 0;
+    CKS(read_status(ctx, &st));
+    CK(cudaMemsetAsync(ctx->gstat, 0, sizeof(long long) * 3, ctx->stream));
+    ctx->mvp_rounds += n_steps * ctx->graph_rounds_fixed + gs[0];
+    ctx->entry_rhs += n_steps * ctx->graph_entries_fixed + (double)ctx->n * (double)ctx->n * gs[1];
+    ctx->launches += n_steps * ctx->graph_launches_fixed + gs[2];
+    return status_to_result(ctx, st);
+  }
   for (int k = 0; k < n_steps; ++k) {
     const unsigned long long step = step0 + (unsigned long long)k;
     CKS(grad_core(ctx, step));
@@ -1661,6 +1928,11 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   ctx->ws_allocs.clear();
   for (ulisse_ctx* sub : ctx->subs) ulisse_destroy(sub);
   ctx->subs.clear();
+  graph_release(ctx);
+  if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+  if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
+  dev_free(reinterpret_cast<void*&>(ctx->chain));
+  dev_free(reinterpret_cast<void*&>(ctx->gstat));
   for (void** p : {reinterpret_cast<void**>(&ctx->b_items), reinterpret_cast<void**>(&ctx->b_kdesc),
                    reinterpret_cast<void**>(&ctx->b_gdesc), reinterpret_cast<void**>(&ctx->b_queue),
                    reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),

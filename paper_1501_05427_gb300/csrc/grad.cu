@@ -248,6 +248,10 @@ struct GradInst {
   static cudaError_t launch(GradLaunch& L, cudaStream_t s) {
     KmvPlan p = plan_split(L.n, BM, M, (int)sizeof(T), L.num_sms * occupancy());
     const size_t need = (size_t)p.n_rb * p.nsplit * kMaxP;
+    if (L.plan_only) {
+      L.need_partials_len = need;
+      return cudaSuccess;
+    }
     if (need > L.partials_len) {
       L.need_partials_len = need;
       return cudaErrorMemoryAllocation;

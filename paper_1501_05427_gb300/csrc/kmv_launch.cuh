@@ -42,6 +42,11 @@ struct KmvInst {
       p.tiles_per_split = 0;
       p.partial_bytes = 0;
     }
+    if (L.plan_only) {
+      L.need_partials_bytes = p.partial_bytes;
+      L.need_counters = p.nsplit > 1 ? p.n_rb : 0;
+      return cudaSuccess;
+    }
     if (p.partial_bytes > L.partials_bytes || (p.nsplit > 1 && p.n_rb > L.counters_len)) {
       // Scratch too small: report what this launch needs; the caller grows it and retries.
       L.need_partials_bytes = p.partial_bytes;

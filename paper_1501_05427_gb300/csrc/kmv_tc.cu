@@ -372,6 +372,11 @@ struct TcInst {
   static cudaError_t launch(TcLaunch& L, cudaStream_t s) {
     KmvPlan p = plan_split(L.n, kTcBM, N, 4, L.num_sms * occupancy());
     const size_t pbytes = p.nsplit > 1 ? (size_t)p.n_rb * p.nsplit * N * kTcBM * 4 : 0;
+    if (L.plan_only) {
+      L.need_partials_bytes = pbytes;
+      L.need_counters = p.nsplit > 1 ? p.n_rb : 0;
+      return cudaSuccess;
+    }
     if (pbytes > L.partials_bytes || (p.nsplit > 1 && p.n_rb > L.counters_len)) {
       L.need_partials_bytes = pbytes;
       L.need_counters = p.n_rb;

@@ -15,9 +15,21 @@ constexpr int kCgNT = 512;
 // a2: probes r_j (column j = 1..nr of B): +-1 from the top bit, or N(0,1) by Box-Muller,
 // element i of probe j from Philox counter (i, j, epoch, 1) keyed by (seed, 0).
 // ------------------------------------------------------------------------------------
+// Step of a chain run from a CUDA graph: the kernels of the graph read the step number,
+// the step size and the trace slot from here (one graph serves every step of the chain);
+// the SGLD update, the graph's last kernel, advances k.
+struct ChainSlot {
+  long long k;                  // index of the step within the chain call
+  unsigned long long step0;     // step number of k = 0
+  const double* eps;            // step sizes, one per k
+  double* trace;                // NULL or p doubles per k
+};
+
 template <typename T>
 __global__ void probes_kernel(T* __restrict__ B, long long ld, long long n, int nr, int kind,
-                              unsigned long long seed, unsigned long long epoch) {
+                              unsigned long long seed, unsigned long long epoch,
+                              const ChainSlot* __restrict__ cs = nullptr, int refresh = 1) {
+  if (cs) epoch = (cs->step0 + (unsigned long long)cs->k) / (unsigned long long)refresh;
   const int j = blockIdx.y + 1;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -50,6 +62,7 @@ struct CgArgs {
   int max_iter;
   int has_s0;
   unsigned long long seed, step;
+  const ChainSlot* cs;   // when set, the step number comes from the chain slot
   int* status;
 };
 
@@ -121,8 +134,9 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
     st.l = 0;
     st.m = 0;
     st.outcome = 0;
-    st.J[0] = draw_J(a.seed, a.step, st.colid, 0, a.beta, a.max_iter);
-    st.J[1] = n_est > 1 ? draw_J(a.seed, a.step, st.colid, 1, a.beta, a.max_iter) : -1;
+    const unsigned long long step = a.cs ? a.cs->step0 + (unsigned long long)a.cs->k : a.step;
+    st.J[0] = draw_J(a.seed, step, st.colid, 0, a.beta, a.max_iter);
+    st.J[1] = n_est > 1 ? draw_J(a.seed, step, st.colid, 1, a.beta, a.max_iter) : -1;
     st.phase = done ? kDone : kPre;
   }
 }
@@ -286,12 +300,11 @@ __global__ void compact_kernel(ColState* __restrict__ st, const ColState* __rest
 // a7: SGLD proposal psi' = psi + eps/2 M (g + grad log p) + sqrt(eps) L xi, L L^T = M,
 // xi_k standard normal from Philox counter (k, 0, step, 3).  One thread.
 // ------------------------------------------------------------------------------------
-__global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__ g,
-                            const double* __restrict__ M, const double* __restrict__ prior,
-                            const double* __restrict__ eps_arr, double eps_scalar, int p,
-                            unsigned long long seed, unsigned long long step,
-                            double* __restrict__ trace, int* __restrict__ status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ inline void sgld_body(double* __restrict__ psi, const double* __restrict__ g,
+                                 const double* __restrict__ M, const double* __restrict__ prior,
+                                 double eps, int p, unsigned long long seed,
+                                 unsigned long long step, double* __restrict__ trace,
+                                 int* __restrict__ status) {
   double Mm[kMaxP * kMaxP], L[kMaxP * kMaxP], xi[kMaxP], v[kMaxP];
   for (int i = 0; i < p; ++i)
     for (int j = 0; j < p; ++j) Mm[i * p + j] = M ? M[i * p + j] : (i == j ? 1.0 : 0.0);
@@ -315,7 +328,6 @@ __global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__
     philox4x64_10((uint64_t)k, 0, step, kPurposeSgld, seed, 0, w);
     xi[k] = box_muller(w[0], w[1]);
   }
-  const double eps = eps_arr ? *eps_arr : eps_scalar;
   for (int i = 0; i < p; ++i) v[i] = g[i] + (prior ? prior[i] : 0.0);
   double out[kMaxP];
   for (int i = 0; i < p; ++i) {
@@ -328,6 +340,62 @@ __global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__
     psi[i] = out[i];
     if (trace) trace[i] = out[i];
   }
+}
+
+__global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__ g,
+                            const double* __restrict__ M, const double* __restrict__ prior,
+                            const double* __restrict__ eps_arr, double eps_scalar, int p,
+                            unsigned long long seed, unsigned long long step,
+                            double* __restrict__ trace, int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  sgld_body(psi, g, M, prior, eps_arr ? *eps_arr : eps_scalar, p, seed, step, trace, status);
+}
+
+// The same update inside a chain graph: step, step size and trace slot from the chain
+// slot, which then moves on to the next step.
+__global__ void sgld_chain_kernel(double* __restrict__ psi, const double* __restrict__ g,
+                                  const double* __restrict__ M, const double* __restrict__ prior,
+                                  int p, unsigned long long seed, ChainSlot* __restrict__ cs,
+                                  int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const long long k = cs->k;
+  sgld_body(psi, g, M, prior, cs->eps[k], p, seed, cs->step0 + (unsigned long long)k,
+            cs->trace ? cs->trace + k * p : nullptr, status);
+  cs->k = k + 1;
+}
+
+// Graph form of compact_kernel: commits the previous iteration's column states (the live
+// list and count are still those of the previous iteration; the count is 0 before the
+// first), rebuilds the list, and sets the graph's loop conditions -- the WHILE body runs
+// again while columns are live, and the SWITCH picks the branch compiled for that many
+// live columns (none when 0).  A round cap (max_iter + 2) stops a loop that would not end.
+// stat: [rounds, sum of live columns over rounds, kernel launches, iterations this call].
+__global__ void compact_graph_kernel(ColState* __restrict__ st, const ColState* __restrict__ st_next,
+                                     int R, int* __restrict__ live, int* __restrict__ n_live,
+                                     cudaGraphConditionalHandle h_loop,
+                                     cudaGraphConditionalHandle h_branch, int chunk_cols,
+                                     int launches_per_chunk, int launches_fixed, int max_rounds,
+                                     long long* __restrict__ stat, int* __restrict__ status) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int n_prev = *n_live;
+  for (int k = 0; k < n_prev; ++k) st[live[k]] = st_next[live[k]];
+  int k = 0;
+  for (int c = 0; c < R; ++c)
+    if (st[c].phase != kDone) live[k++] = c;
+  const long long it = stat[3]++;
+  if (k > 0 && it >= max_rounds) {
+    atomicOr(status, kStatusMaxIter);
+    k = 0;
+  }
+  *n_live = k;
+  stat[2] += 1;
+  if (k > 0) {
+    stat[0] += 1;
+    stat[1] += k;
+    stat[2] += launches_fixed + (long long)launches_per_chunk * ((k + chunk_cols - 1) / chunk_cols);
+  }
+  cudaGraphSetConditional(h_loop, k > 0 ? 1u : 0u);
+  cudaGraphSetConditional(h_branch, k > 0 ? (unsigned)(k - 1) : (unsigned)R);
 }
 
 // Element-type conversion between caller buffers and the context's (FP64 contexts).

@@ -214,6 +214,7 @@ struct KmvLaunch {
   // cudaErrorMemoryAllocation without launching).
   size_t need_partials_bytes;
   int need_counters;
+  bool plan_only;        // only fill need_* (no launch): sizing scratch ahead of a capture
 };
 
 struct GradLaunch {
@@ -235,6 +236,7 @@ struct GradLaunch {
   int* status;
   int num_sms;
   size_t need_partials_len;  // set when partials_len is too small
+  bool plan_only;            // only fill need_partials_len (no launch)
 };
 
 // Mixed-precision (tcgen05) K V launch: operands prepared by launch_prescale_tc.
@@ -261,6 +263,7 @@ struct TcLaunch {
   int num_sms;
   size_t need_partials_bytes;
   int need_counters;
+  bool plan_only;        // only fill need_* (no launch): sizing scratch ahead of a capture
 };
 
 // Launchers (return cudaSuccess or the launch error).

@@ -34,6 +34,7 @@ EXPORTED = [
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
+    "ulisse_set_graph",
 ]
 
 
@@ -125,6 +126,7 @@ def load():
     lib.ulisse_batch_kmv.argtypes = [P, P, P, I, P]
     lib.ulisse_batch_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_batch_sgld_step.argtypes = [P, P, D, U64, P]
+    lib.ulisse_set_graph.argtypes = [P, I]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -325,6 +327,10 @@ class Context:
         self._check(self._lib.ulisse_ws_x0(self._h, _hptr(psi), int(bool(bf16)),
                                            ctypes.c_void_p(x0.data_ptr())))
         return x0
+
+    def set_graph(self, enable=True):
+        """sgld_chain: one CUDA-graph launch per step (True) or the host loop (False)."""
+        self._check(self._lib.ulisse_set_graph(self._h, int(bool(enable))))
 
     def counters(self):
         """(K V rounds, generated entries x right-hand sides, kernel launches) so far."""
@@ -539,3 +545,7 @@ def ulisse_batch_grad(ctx: BatchContext, psi, step=0):
 
 def ulisse_batch_sgld_step(ctx: BatchContext, psi, eps_t, step):
     return ctx.sgld_step(psi, eps_t, step)
+
+
+def ulisse_set_graph(ctx: Context, enable=True):
+    ctx.set_graph(enable)
