@@ -8,6 +8,12 @@ C ABI.  Prints one JSON line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
+The headline is the chosen path -- tensor-core (tcgen05) mixed-precision K V, every step one
+CUDA-graph launch -- in SGLD steps/s; the plain FP32 path (SIMT K V, same graph form) is timed
+the same way beside it, and both report K V entry*RHS/s from an event-timed pass.  The
+gradient error of both paths at the same parameters is the committed measurement in
+profiles/grad_error_census_like.txt (tests/test_gpu_grad_error.py).
+
 --impl reference times the FP64 CPU oracle on the host cores instead (a bounded sample of
 the same workload, scaled to SGLD steps/s).  With N > 1 (torchrun) every rank runs an
 independent chain (replicas: the method's path for one problem runs on one GPU).
@@ -37,11 +43,22 @@ EPS_T = 1e-4
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
 WORK_FILE = os.path.join(ROOT, "profiles", "census_like_step_work.txt")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "kmv_census_like_traffic.txt")
-KMV_SOURCES = ["paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
-               "paper_1501_05427_gb300/csrc/kmv_launch.cuh",
-               "paper_1501_05427_gb300/csrc/kmv_f32.cu",
-               "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]
+GRAD_ERROR_FILE = os.path.join(ROOT, "profiles", "grad_error_census_like.txt")
+# per K V kernel: its ncu traffic summary and the sources whose hash it was taken for
+KMV_KERNELS = {
+    "fp32": ("kmv_kernel (tile-generating K V, FP32 SIMT)",
+             os.path.join(ROOT, "profiles", "kmv_census_like_traffic.txt"),
+             ["paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
+              "paper_1501_05427_gb300/csrc/kmv_launch.cuh",
+              "paper_1501_05427_gb300/csrc/kmv_f32.cu",
+              "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
+    "mixed": ("kmv_tc_kernel (tile-generating K V, tcgen05 BF16x3, FP32 accumulation)",
+              os.path.join(ROOT, "profiles", "kmv_tc_census_like_traffic.txt"),
+              ["paper_1501_05427_gb300/csrc/kmv_tc.cu",
+               "paper_1501_05427_gb300/csrc/tc_common.cuh",
+               "paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
+               "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
+}
 
 
 def parse_args():
@@ -50,12 +67,17 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target host time of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--path", choices=["fp32", "mixed"], default="fp32",
-                    help="K V path: FP32 SIMT or tensor-core mixed precision")
+    ap.add_argument("--path", choices=["fp32", "mixed"], default="mixed",
+                    help="chosen K V path: tensor-core mixed precision or FP32 SIMT")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip timing the plain FP32 path beside the chosen one")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="run the steps from the host loop instead of one graph launch each")
+    ap.add_argument("--profile-steps", type=int, default=8,
+                    help="steps of the event-timed pass (per-launch K V times)")
     return ap.parse_args()
 
 
@@ -71,9 +93,9 @@ def _kv_file(path):
     return out
 
 
-def kmv_source_hash():
+def kmv_source_hash(path="fp32"):
     h = hashlib.sha256()
-    for f in KMV_SOURCES:
+    for f in KMV_KERNELS[path][2]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -247,6 +269,61 @@ def run_reference(args):
     return 0
 
 
+def _timed_steps(ctx, dev, stream, psi0, K, W, step_base, flush, barrier, sampler=None):
+    """W untimed steps, then K steps each bracketed by CUDA events on the library's stream,
+    with an L2 flush (outside the spans) before each."""
+    import torch
+    psi_dev = torch.tensor(psi0, dtype=torch.float64, device=dev)
+    eps_dev = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
+    for k in range(W):
+        ctx.sgld_chain(psi_dev, eps_dev[:1], step0=step_base + k)
+    c0 = ctx.counters()
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+    if sampler:
+        sampler.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    rounds = []
+    for k in range(K):
+        flush.zero_()
+        events[k][0].record(stream)
+        ctx.sgld_chain(psi_dev, eps_dev[k:k + 1], step0=step_base + W + k)
+        events[k][1].record(stream)
+        rounds.append(ctx.counters()[0])
+    torch.cuda.synchronize(dev)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+    c1 = ctx.counters()
+    rounds = [b - a for a, b in zip([c0[0]] + rounds[:-1], rounds)]
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    return {"step_ms": step_ms, "total_ms": sum(step_ms), "rounds": rounds,
+            "counters": tuple(b - a for a, b in zip(c0, c1)), "clocks": clocks}
+
+
+def _profile_pass(ctx, dev, psi0, P, step_base, n, R):
+    """P steps with event timing of every O(n^2) launch (this runs the host loop)."""
+    import torch
+    psi_dev = torch.tensor(psi0, dtype=torch.float64, device=dev)
+    eps_dev = torch.full((max(P, 1),), EPS_T, dtype=torch.float64, device=dev)
+    ctx.profile_enable(True)
+    c0 = ctx.counters()
+    ctx.sgld_chain(psi_dev, eps_dev[:P], step0=step_base)
+    c1 = ctx.counters()
+    prof = ctx.profile_read(reset=True)
+    ctx.profile_enable(False)
+    grad_entries = float(n) * n * R
+    mvp_erhs = (c1[1] - c0[1]) - grad_entries * P
+    return {
+        "kmv_ms": prof["kmv_ms"], "kmv_flop": prof["kmv_flop"], "kmv_launches": prof["kmv_launches"],
+        "grad_ms": prof["grad_ms"], "grad_flop": prof["grad_flop"],
+        "mvp_entry_rhs": mvp_erhs, "rounds": c1[0] - c0[0], "steps": P,
+        "kv_entry_rhs_per_s": mvp_erhs / (prof["kmv_ms"] / 1e3) if prof["kmv_ms"] > 0 else None,
+        "kmv_tflops": (prof["kmv_flop"] / (prof["kmv_ms"] / 1e3) / 1e12
+                       if prof["kmv_ms"] > 0 else None),
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -259,135 +336,138 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     prob = w.census_like()
     n, d = prob.n, prob.d
-    p = d + 2
-    prec = u.PREC_MIXED if args.path == "mixed" else u.PREC_FP32
-    cfg = u.ulisse_config_default(n_probes=N_PROBES, probe_kind=u.PROBE_RADEMACHER, q=1.0,
-                                  beta=1.0, eps=1e-8, max_iter=1000, seed=20150123 + rank,
-                                  precision=prec)
+    p, R = d + 2, 1 + N_PROBES
     X = torch.from_numpy(prob.X).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
     stream = torch.cuda.current_stream(dev)
-    ctx = u.Context(X, y, cfg, stream=stream)
     K, W = args.steps, args.warmup
-    psi_dev = torch.tensor(prob.psi_true, dtype=torch.float64, device=dev)
-    eps_dev = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    for k in range(W):
-        ctx.sgld_chain(psi_dev, eps_dev[:1], step0=k)
-    ctx.profile_enable(True)
-    rounds0, erhs0, launches0 = ctx.counters()
-    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(K)]
-    sampler = ClockSampler(local)
-    sampler.start()
-    barrier()
-    torch.cuda.synchronize(dev)
-    rounds_per_step = []
-    for k in range(K):
-        flush.zero_()                     # L2 flush, outside the timed spans
-        events[k][0].record(stream)
-        ctx.sgld_chain(psi_dev, eps_dev[k:k + 1], step0=W + k)
-        events[k][1].record(stream)
-        rounds_per_step.append(ctx.counters()[0])
-    torch.cuda.synchronize(dev)
-    rounds_per_step = [b - a for a, b in zip([rounds0] + rounds_per_step[:-1], rounds_per_step)]
-    barrier()
-    clocks = sampler.stop()
-    step_ms = [a.elapsed_time(b) for a, b in events]
-    total_ms = sum(step_ms)
-    rounds1, erhs1, launches1 = ctx.counters()
-    prof = ctx.profile_read(reset=True)
-    ctx.profile_enable(False)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * K / (total_ms / 1000.0)
+    def make_ctx(path):
+        prec = u.PREC_MIXED if path == "mixed" else u.PREC_FP32
+        cfg = u.ulisse_config_default(n_probes=N_PROBES, probe_kind=u.PROBE_RADEMACHER, q=1.0,
+                                      beta=1.0, eps=1e-8, max_iter=1000,
+                                      seed=20150123 + rank, precision=prec)
+        c = u.Context(X, y, cfg, stream=stream)
+        c.set_graph(not args.no_graph)
+        return c
 
-    # end to end through the host-buffer API: psi in, (psi, g) out every step
-    e2e_steps = args.e2e_steps
+    def max_over_ranks(v):
+        if world > 1:
+            t = torch.tensor([v], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    # chosen path: the timed region
+    ctx = make_ctx(args.path)
+    res = _timed_steps(ctx, dev, stream, prob.psi_true, K, W, 0, flush, barrier,
+                       ClockSampler(local))
+    total_ms = max_over_ranks(res["total_ms"])
+    value = world * K / (total_ms / 1000.0)
+    rounds, erhs, launches = res["counters"]
+
+    # per-launch K V and gradient times (event-timed pass of the same workload)
+    prof = _profile_pass(ctx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
+
+    # end to end through the host-buffer API (psi in, psi and g out every step), replaying
+    # exactly the timed steps: same start, same step numbers, hence the same draws and rounds
     psi_h = prob.psi_true.copy()
-    ctx.sgld_step(psi_h, EPS_T, step=10_000)          # warm
+    for k in range(W):
+        psi_h, _ = ctx.sgld_step(psi_h, EPS_T, step=k)
     barrier()
     torch.cuda.synchronize(dev)
     r_e0 = ctx.counters()[0]
     t0 = time.perf_counter()
-    for k in range(e2e_steps):
-        psi_h, g_h = ctx.sgld_step(psi_h, EPS_T, step=W + K + 1 + k)
+    for k in range(K):
+        psi_h, g_h = ctx.sgld_step(psi_h, EPS_T, step=W + k)
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    e2e_rounds = (ctx.counters()[0] - r_e0) / max(e2e_steps, 1)
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * e2e_steps / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_rounds = (ctx.counters()[0] - r_e0) / max(K, 1)
+    e2e_value = world * K / e2e_s
+    ctx.close()
 
-    mvp_rounds = (rounds1 - rounds0) / K
-    grad_entries = float(n) * n
-    mvp_erhs = (erhs1 - erhs0) / K - grad_entries * (1 + N_PROBES)
-    kmv_tflops = prof["kmv_flop"] / (prof["kmv_ms"] / 1e3) / 1e12 if prof["kmv_ms"] > 0 else None
+    # plain FP32 path, same workload, same form
+    plain = None
+    if not args.no_plain and args.path != "fp32":
+        pctx = make_ctx("fp32")
+        pres = _timed_steps(pctx, dev, stream, prob.psi_true, K, W, 0, flush, barrier)
+        pprof = _profile_pass(pctx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
+        pctx.close()
+        ptotal = max_over_ranks(pres["total_ms"])
+        plain = {"value": world * K / (ptotal / 1000.0), "unit": "steps/s",
+                 "ms_per_step": ptotal / K,
+                 "mvp_rounds_per_step": pres["counters"][0] / K,
+                 "kv_entry_rhs_per_s": pprof["kv_entry_rhs_per_s"],
+                 "kmv_ms_per_round": (pprof["kmv_ms"] / pprof["rounds"] if pprof["rounds"] else None),
+                 "kernel": KMV_KERNELS["fp32"][0]}
+
+    name, traffic_file, _ = KMV_KERNELS[args.path]
     traffic = None
-    tf = _kv_file(TRAFFIC_FILE)
-    if tf and tf.get("kmv_source_hash") == kmv_source_hash() and prof["kmv_launches"] > 0:
-        # captured launch: bytes per launch for R_cap right-hand sides; scale to this run's
-        # mean right-hand sides per launch (X^ and V tiles grow with R, X^ does not)
+    tf = _kv_file(traffic_file)
+    if tf and tf.get("kmv_source_hash") == kmv_source_hash(args.path):
         traffic = float(tf["dram_bytes_per_launch"])
+    kmv_tflops = prof["kmv_tflops"]
     roofline = {
         "bound": "alu",
-        "kernel": ("kmv_tc_kernel (tile-generating K V, tcgen05)" if args.path == "mixed"
-                   else "kmv_kernel (tile-generating K V, FP32 SIMT)"),
+        "kernel": name,
         "achieved": kmv_tflops,
         "peak": FP32_FMA_PEAK_TFLOPS,
         "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz max SM clock",
         "unit": "TFLOP/s",
         "frac": (kmv_tflops / FP32_FMA_PEAK_TFLOPS) if kmv_tflops else None,
         "traffic": traffic,
+        "flop_per_entry": "3d + 2 + 2R (distance, kernel value, contraction)",
+        "measured_in": "event-timed pass of %d steps (host loop, one event pair per launch)"
+                       % prof["steps"],
         "kmv_launches": prof["kmv_launches"],
-        "kmv_ms_per_step": prof["kmv_ms"] / K,
-        "grad_ms_per_step": prof["grad_ms"] / K,
+        "kmv_ms_per_round": prof["kmv_ms"] / prof["rounds"] if prof["rounds"] else None,
+        "grad_ms_per_step": prof["grad_ms"] / prof["steps"],
         "grad_tflops": (prof["grad_flop"] / (prof["grad_ms"] / 1e3) / 1e12
                         if prof["grad_ms"] > 0 else None),
-        "share_of_step": (prof["kmv_ms"] / total_ms) if world == 1 else None,
     }
+    grad_err = _kv_file(GRAD_ERROR_FILE)
     line = {
         "metric": "SGLD steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16x3/f32" if args.path == "mixed" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "d": d, "n_probes": N_PROBES, "q": 1.0,
                    "beta": 1.0, "eps_t": EPS_T,
-                   "path": ("tcgen05 mixed K V (3xTF32 cross term, 3xBF16 contraction)"
+                   "path": ("tcgen05 mixed K V (FP32 kernel values, 3xBF16 contraction)"
                             if args.path == "mixed" else "fp32 SIMT K V"),
+                   "step_form": "host loop" if args.no_graph else "one CUDA graph launch per step",
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
-        "kv_throughput": {"value": (mvp_erhs * K) / (prof["kmv_ms"] / 1e3)
-                          if prof["kmv_ms"] > 0 else None, "unit": "entry·RHS/s"},
-        "mvp_rounds_per_step": mvp_rounds,
-        "rounds_per_step": rounds_per_step,
+        "kv_throughput": {"value": prof["kv_entry_rhs_per_s"], "unit": "entry·RHS/s",
+                          "plain_fp32": plain["kv_entry_rhs_per_s"] if plain else None},
+        "plain_fp32": plain,
+        "gradient_error": ({k: grad_err[k] for k in grad_err} if grad_err else None),
+        "mvp_rounds_per_step": rounds / K,
+        "rounds_per_step": res["rounds"],
         "roofline": roofline,
-        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * p,
-                "d2h_bytes_per_step": 16 * p, "mvp_rounds_per_step": e2e_rounds,
-                "api": "ulisse_sgld_step (host psi in, host psi and g out)"},
-        "gpu_launches": int(launches1 - launches0),
-        "clocks": clocks,
-        "step_ms": step_ms,
+        "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * p + 8 + 32,
+                "d2h_bytes_per_step": 16 * p + 32 + 4, "mvp_rounds_per_step": e2e_rounds,
+                "api": "ulisse_sgld_step (host psi in, host psi and g out)",
+                "steps": "the timed steps replayed (same start and step numbers)"},
+        "gpu_launches": int(launches),
+        "clocks": res["clocks"],
+        "step_ms": res["step_ms"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        work = {"mvp_entry_rhs": mvp_erhs, "grad_entries": grad_entries,
-                "mvp_rounds": mvp_rounds}
+        work = {"mvp_entry_rhs": erhs / K - float(n) * n * R, "grad_entries": float(n) * n,
+                "mvp_rounds": rounds / K}
         cb = oracle_sample(prob, work, args.cpu_seconds)
         line["cpu_baseline"] = {"value": cb["steps_per_s"], "unit": "steps/s",
                                 "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
                                 "kv_entry_rhs_per_s": cb["kv_entry_rhs_per_s"]}
-        line["work_per_step"] = {"mvp_entry_rhs_per_step": mvp_erhs,
-                                 "grad_entries_per_step": grad_entries,
-                                 "mvp_rounds_per_step": mvp_rounds}
-    ctx.close()
+        line["work_per_step"] = {"mvp_entry_rhs_per_step": work["mvp_entry_rhs"],
+                                 "grad_entries_per_step": work["grad_entries"],
+                                 "mvp_rounds_per_step": work["mvp_rounds"]}
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -91,6 +91,10 @@ struct ulisse_ctx {
   long long graph_key = -1;   // configuration the graph was captured for
   ChainSlot* chain = nullptr; // device
   long long* gstat = nullptr; // device: rounds, sum of live columns, launches, rounds this step
+  long long* h_gstat = nullptr;  // pinned copy
+  double* eps_one = nullptr;  // device step size of a single graph step
+  bool m_identity = false;    // M_dev holds the identity (the graph's default M)
+  bool prior_zero = false;    // prior_dev holds zeros
   long long graph_launches_fixed = 0;  // kernel launches per step outside the CG loop
   double graph_entries_fixed = 0.0;    // entries x right-hand sides per step outside the loop
   long long graph_rounds_fixed = 0;
@@ -778,6 +782,14 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
 
 extern "C" {
 
+// the step graph (defined with ulisse_sgld_chain)
+static bool graph_usable(const ulisse_ctx* ctx);
+static ulisse_status graph_alloc(ulisse_ctx* ctx);
+static ulisse_status graph_prepare(ulisse_ctx* ctx, const double* M, const double* prior,
+                                   unsigned long long step0, const double* eps_dev,
+                                   double* trace_dev);
+static void graph_fold_counters(ulisse_ctx* ctx, int n_steps);
+
 void ulisse_config_default(ulisse_config* cfg) {
   if (!cfg) return;
   std::memset(cfg, 0, sizeof(*cfg));
@@ -942,12 +954,14 @@ static ulisse_status upload_M_prior(ulisse_ctx* ctx, const double* M, const doub
       if (!std::isfinite(M[i])) return fail(ctx, ULISSE_ERR_ARG, "M not finite");
     CK(cudaMemcpyAsync(ctx->M_dev, M, sizeof(double) * p * p, cudaMemcpyHostToDevice,
                        ctx->stream));
+    ctx->m_identity = false;
     *Md = ctx->M_dev;
   }
   if (prior) {
     if (!finite_psi(prior, p)) return fail(ctx, ULISSE_ERR_ARG, "prior_grad not finite");
     CK(cudaMemcpyAsync(ctx->prior_dev, prior, sizeof(double) * p, cudaMemcpyHostToDevice,
                        ctx->stream));
+    ctx->prior_zero = false;
     *pd = ctx->prior_dev;
   }
   return ULISSE_OK;
@@ -962,6 +976,27 @@ ulisse_status ulisse_sgld_step(ulisse_ctx* ctx, double* psi_inout, double eps_t,
   const double *Md, *pd;
   CKS(upload_M_prior(ctx, M, prior_grad, &Md, &pd));
   CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  if (graph_usable(ctx)) {
+    // one launch of the step graph; the step size travels through the device
+    CKS(graph_alloc(ctx));
+    CK(cudaMemcpyAsync(ctx->eps_one, &eps_t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CKS(graph_prepare(ctx, M, prior_grad, step, ctx->eps_one, nullptr));
+    CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_gstat, ctx->gstat, sizeof(long long) * 4, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    int st = 0;
+    CKS(read_status(ctx, &st));
+    graph_fold_counters(ctx, 1);
+    ulisse_status r = status_to_result(ctx, st);
+    if (r == ULISSE_ERR_ARG) return r;
+    CK(cudaMemcpyAsync(psi_inout, ctx->psi_dev, sizeof(double) * (ctx->d + 2),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    if (g_out)
+      CK(cudaMemcpyAsync(g_out, ctx->g_dev, sizeof(double) * (ctx->d + 2),
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return r;
+  }
   CKS(grad_core(ctx, step));
   sgld_kernel<<<1, 32, 0, ctx->stream>>>(ctx->psi_dev, ctx->g_dev, Md, pd, nullptr, eps_t,
                                          ctx->d + 2, ctx->cfg.seed, step, nullptr,
@@ -1178,6 +1213,54 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
   return ULISSE_OK;
 }
 
+static bool graph_usable(const ulisse_ctx* ctx) {
+  return ctx->graph_enabled && !ctx->prof && !ctx->ws_record;
+}
+
+static ulisse_status graph_alloc(ulisse_ctx* ctx) {
+  if (ctx->chain) return ULISSE_OK;
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->chain), sizeof(ChainSlot)));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gstat), sizeof(long long) * 4));
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->eps_one), sizeof(double)));
+  if (cudaMallocHost(&ctx->h_gstat, sizeof(long long) * 4) != cudaSuccess)
+    return fail(ctx, ULISSE_ERR_NOMEM, "cudaMallocHost failed");
+  return ULISSE_OK;
+}
+
+// Identity M / zero prior in the context's buffers when not given (the graph always reads
+// them), the chain slot for the coming launches, and the graph itself if it is stale.
+static ulisse_status graph_prepare(ulisse_ctx* ctx, const double* M, const double* prior,
+                                   unsigned long long step0, const double* eps_dev,
+                                   double* trace_dev) {
+  const int p = ctx->d + 2;
+  if (!M && !ctx->m_identity) {
+    std::vector<double> I((size_t)p * p, 0.0);
+    for (int i = 0; i < p; ++i) I[(size_t)i * p + i] = 1.0;
+    CK(cudaMemcpyAsync(ctx->M_dev, I.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    ctx->m_identity = true;
+  }
+  if (!prior && !ctx->prior_zero) {
+    CK(cudaMemsetAsync(ctx->prior_dev, 0, sizeof(double) * p, ctx->stream));
+    ctx->prior_zero = true;
+  }
+  CKS(graph_alloc(ctx));
+  const ChainSlot cs{0, step0, eps_dev, trace_dev};
+  CK(cudaMemcpyAsync(ctx->chain, &cs, sizeof(ChainSlot), cudaMemcpyHostToDevice, ctx->stream));
+  const int s0 = (ctx->ws_use && ctx->ws_trained) ? 1 : 0;
+  if (ctx->graph_key != s0) CKS(graph_build(ctx, s0));
+  return ULISSE_OK;
+}
+
+// Host counters after n_steps graph launches (h_gstat already copied back and synchronised).
+static void graph_fold_counters(ulisse_ctx* ctx, int n_steps) {
+  const long long* gs = ctx->h_gstat;
+  ctx->mvp_rounds += n_steps * ctx->graph_rounds_fixed + gs[0];
+  ctx->entry_rhs += n_steps * ctx->graph_entries_fixed + (double)ctx->n * (double)ctx->n * gs[1];
+  ctx->launches += n_steps * ctx->graph_launches_fixed + gs[2];
+  cudaMemsetAsync(ctx->gstat, 0, sizeof(long long) * 3, ctx->stream);
+}
+
 ulisse_status ulisse_set_graph(ulisse_ctx* ctx, int enable) {
   if (!ctx) return ULISSE_ERR_ARG;
   if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
@@ -1199,33 +1282,16 @@ ulisse_status ulisse_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* 
                      ctx->stream));
   // Each step as one launch of the step graph, unless the event timing is on (it times
   // single launches) or warm-start pairs are being recorded (host-side bookkeeping).
-  if (ctx->graph_enabled && !ctx->prof && !ctx->ws_record && n_steps > 0) {
-    if (!M) {
-      std::vector<double> I((size_t)p * p, 0.0);
-      for (int i = 0; i < p; ++i) I[(size_t)i * p + i] = 1.0;
-      CK(cudaMemcpyAsync(ctx->M_dev, I.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
-                         ctx->stream));
-    }
-    if (!prior_grad) CK(cudaMemsetAsync(ctx->prior_dev, 0, sizeof(double) * p, ctx->stream));
-    if (!ctx->chain) {
-      CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->chain), sizeof(ChainSlot)));
-      CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->gstat), sizeof(long long) * 4));
-    }
-    const ChainSlot cs{0, step0, eps_dev, trace_dev};
-    CK(cudaMemcpyAsync(ctx->chain, &cs, sizeof(ChainSlot), cudaMemcpyHostToDevice, ctx->stream));
-    const int s0 = (ctx->ws_use && ctx->ws_trained) ? 1 : 0;
-    if (ctx->graph_key != s0) CKS(graph_build(ctx, s0));
+  if (graph_usable(ctx) && n_steps > 0) {
+    CKS(graph_prepare(ctx, M, prior_grad, step0, eps_dev, trace_dev));
     for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
     CK(cudaMemcpyAsync(psi_dev, ctx->psi_dev, sizeof(double) * p, cudaMemcpyDeviceToDevice,
                        ctx->stream));
-    long long gs[4] = {0, 0, 0, 0};
-    CK(cudaMemcpyAsync(gs, ctx->gstat, sizeof(gs), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_gstat, ctx->gstat, sizeof(long long) * 4, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     int st = 0;
     CKS(read_status(ctx, &st));
-    CK(cudaMemsetAsync(ctx->gstat, 0, sizeof(long long) * 3, ctx->stream));
-    ctx->mvp_rounds += n_steps * ctx->graph_rounds_fixed + gs[0];
-    ctx->entry_rhs += n_steps * ctx->graph_entries_fixed + (double)ctx->n * (double)ctx->n * gs[1];
-    ctx->launches += n_steps * ctx->graph_launches_fixed + gs[2];
+    graph_fold_counters(ctx, n_steps);
     return status_to_result(ctx, st);
   }
   for (int k = 0; k < n_steps; ++k) {
@@ -1933,6 +1999,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   if (ctx->cap_stream2) cudaStreamDestroy(ctx->cap_stream2);
   dev_free(reinterpret_cast<void*&>(ctx->chain));
   dev_free(reinterpret_cast<void*&>(ctx->gstat));
+  dev_free(reinterpret_cast<void*&>(ctx->eps_one));
+  if (ctx->h_gstat) cudaFreeHost(ctx->h_gstat);
   for (void** p : {reinterpret_cast<void**>(&ctx->b_items), reinterpret_cast<void**>(&ctx->b_kdesc),
                    reinterpret_cast<void**>(&ctx->b_gdesc), reinterpret_cast<void**>(&ctx->b_queue),
                    reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),
