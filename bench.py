@@ -64,7 +64,7 @@ KMV_KERNELS = {
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -76,6 +76,8 @@ def parse_args():
                     help="skip timing the plain FP32 path beside the chosen one")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the steps from the host loop instead of one graph launch each")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the K V autotuner (untuned launch configurations)")
     ap.add_argument("--profile-steps", type=int, default=8,
                     help="steps of the event-timed pass (per-launch K V times)")
     return ap.parse_args()
@@ -301,6 +303,20 @@ def _timed_steps(ctx, dev, stream, psi0, K, W, step_base, flush, barrier, sample
             "counters": tuple(b - a for a, b in zip(c0, c1)), "clocks": clocks}
 
 
+def _fit_step_time(step_ms, rounds):
+    """Least-squares step_ms = fixed + per_round * rounds over the timed steps: the two paths
+    follow different CG trajectories (different round counts), so they are also compared
+    at the same number of rounds."""
+    import numpy as np
+    r = np.asarray(rounds, dtype=np.float64)
+    t = np.asarray(step_ms, dtype=np.float64)
+    if len(r) < 3 or np.ptp(r) == 0:
+        return None
+    A = np.column_stack([np.ones_like(r), r])
+    (a, b), *_ = np.linalg.lstsq(A, t, rcond=None)
+    return {"fixed_ms": float(a), "ms_per_round": float(b)}
+
+
 def _profile_pass(ctx, dev, psi0, P, step_base, n, R):
     """P steps with event timing of every O(n^2) launch (this runs the host loop)."""
     import torch
@@ -347,6 +363,8 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
+    tuned = {}
+
     def make_ctx(path):
         prec = u.PREC_MIXED if path == "mixed" else u.PREC_FP32
         cfg = u.ulisse_config_default(n_probes=N_PROBES, probe_kind=u.PROBE_RADEMACHER, q=1.0,
@@ -354,6 +372,8 @@ def run_ours(args):
                                       seed=20150123 + rank, precision=prec)
         c = u.Context(X, y, cfg, stream=stream)
         c.set_graph(not args.no_graph)
+        if not args.no_tune:
+            tuned[path] = c.autotune(prob.psi_true, R, reps=3)
         return c
 
     def max_over_ranks(v):
@@ -399,13 +419,23 @@ def run_ours(args):
         pprof = _profile_pass(pctx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
         pctx.close()
         ptotal = max_over_ranks(pres["total_ms"])
+        pfit = _fit_step_time(pres["step_ms"], pres["rounds"])
         plain = {"value": world * K / (ptotal / 1000.0), "unit": "steps/s",
                  "ms_per_step": ptotal / K,
                  "mvp_rounds_per_step": pres["counters"][0] / K,
+                 "step_time_fit": pfit,
                  "kv_entry_rhs_per_s": pprof["kv_entry_rhs_per_s"],
                  "kmv_ms_per_round": (pprof["kmv_ms"] / pprof["rounds"] if pprof["rounds"] else None),
                  "kernel": KMV_KERNELS["fp32"][0]}
 
+    fit = _fit_step_time(res["step_ms"], res["rounds"])
+    at_equal = None
+    if plain and fit and plain.get("step_time_fit"):
+        r_bar = rounds / K
+        t_c = fit["fixed_ms"] + fit["ms_per_round"] * r_bar
+        t_p = plain["step_time_fit"]["fixed_ms"] + plain["step_time_fit"]["ms_per_round"] * r_bar
+        at_equal = {"rounds_per_step": r_bar, "chosen_steps_per_s": 1000.0 / t_c,
+                    "plain_fp32_steps_per_s": 1000.0 / t_p, "speedup": t_p / t_c}
     name, traffic_file, _ = KMV_KERNELS[args.path]
     traffic = None
     tf = _kv_file(traffic_file)
@@ -446,8 +476,13 @@ def run_ours(args):
         "kv_throughput": {"value": prof["kv_entry_rhs_per_s"], "unit": "entry·RHS/s",
                           "plain_fp32": plain["kv_entry_rhs_per_s"] if plain else None},
         "plain_fp32": plain,
+        "autotune": ({path: {"tuned_over_untuned_ms": [round(e["ms"] / e["ms_default"], 3)
+                                                      for e in tab]}
+                      for path, tab in tuned.items()} if tuned else None),
         "gradient_error": ({k: grad_err[k] for k in grad_err} if grad_err else None),
         "mvp_rounds_per_step": rounds / K,
+        "step_time_fit": fit,
+        "at_equal_rounds": at_equal,
         "rounds_per_step": res["rounds"],
         "roofline": roofline,
         "e2e": {"value": e2e_value, "unit": "steps/s", "h2d_bytes_per_step": 8 * p + 8 + 32,

@@ -368,6 +368,27 @@ ulisse_status ulisse_batch_sgld_step(ulisse_ctx *ctx, double *psi_inout, double 
  * a call that reallocated the context's buffers. */
 ulisse_status ulisse_set_graph(ulisse_ctx *ctx, int enable);
 
+/* Autotuned K V launch configuration for one live column count. */
+typedef struct {
+    int live_cols;           /* columns of the product */
+    int width;               /* compiled column count (SIMT) or MMA N (tensor cores) used */
+    int rows_per_thread;     /* SIMT rows per thread (0 on the tensor-core path) */
+    int nsplit;              /* j-range split count forced (0: the launch plan's choice) */
+    float ms;                /* median time of the chosen configuration */
+    float ms_default;        /* median time of the untuned configuration */
+} ulisse_tune_entry;
+
+/* Time, for every live column count 1..max_cols (<= 32), the candidate K V configurations
+ * on this context's data -- compiled column counts, rows per thread, j-range splits -- with
+ * CUDA events on the context's stream (median of `reps` launches each), and use the
+ * fastest from then on (the untuned choice is always a candidate).  psi: host, the
+ * parameters to tune at (they set the data layout only; any valid psi).  out: NULL or
+ * max_cols entries.  The tuning launches are not counted as the method's work.  Results
+ * change only in the summation order of the split j range (the last bits).
+ * FP32 and mixed contexts. */
+ulisse_status ulisse_autotune(ulisse_ctx *ctx, const double *psi, int max_cols, int reps,
+                              ulisse_tune_entry *out);
+
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);
 

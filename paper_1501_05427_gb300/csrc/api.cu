@@ -81,6 +81,12 @@ struct ulisse_ctx {
 
   int meta_grad_R = -1;       // column count the gradient's column metadata was uploaded for
 
+  // autotuned K V launch configuration per live column count (ulisse_autotune); index
+  // nl - 1, empty until tuned
+  struct KmvTune { int width, tm, nsplit; float ms, ms_default; };
+  std::vector<KmvTune> tune;
+  int last_nsplit = 1;        // split count of the last K V launch (or plan)
+
   // CUDA graph of one SGLD step (ulisse_sgld_chain)
   bool planning = false;      // launch helpers only size their scratch
   bool capturing = false;     // launch helpers are being captured: no host-side counting
@@ -316,9 +322,14 @@ static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap,
     L.params = ctx->params;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
+    if ((int)ctx->tune.size() >= L.R && ctx->tune[L.R - 1].width > 0) {
+      L.n_min = ctx->tune[L.R - 1].width;
+      L.nsplit = ctx->tune[L.R - 1].nsplit;
+    }
     if (ctx->planning) {
       L.plan_only = true;
       cudaError_t e = launch_kmv_tc(L, ctx->stream);
+      ctx->last_nsplit = L.planned_nsplit;
       if (e != cudaSuccess)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("tensor-core K V plan: ") + cudaGetErrorString(e));
       CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
@@ -375,9 +386,15 @@ static ulisse_status run_kmv(ulisse_ctx* ctx, const void* V, const int* vmap, in
     L.tm = ctx->cfg.kmv_rows_per_thread;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
+    if (mode == kModeK && (int)ctx->tune.size() >= L.R && ctx->tune[L.R - 1].width > 0) {
+      L.r_min = ctx->tune[L.R - 1].width;
+      L.tm = ctx->tune[L.R - 1].tm;
+      L.nsplit = ctx->tune[L.R - 1].nsplit;
+    }
     if (ctx->planning) {
       L.plan_only = true;
       cudaError_t e = ctx->f64 ? launch_kmv_f64(L, ctx->stream) : launch_kmv_f32(L, ctx->stream);
+      ctx->last_nsplit = L.planned_nsplit;
       if (e != cudaSuccess)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("K V plan: ") + cudaGetErrorString(e));
       CKS(grow_kmv_scratch(ctx, L.need_partials_bytes, L.need_counters));
@@ -1936,6 +1953,125 @@ ulisse_status ulisse_batch_sgld_step(ulisse_ctx* ctx, double* psi_inout, double 
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return r;
+}
+
+// ---------------------------------------------------------------------------------------
+// Autotuner: for every live column count, the K V launch configuration that runs fastest
+// on this context's data and device, timed with CUDA events on the context's stream.
+// ---------------------------------------------------------------------------------------
+// Median time of `reps` K V launches over nl columns in the given configuration (width 0:
+// the default choices); *nsplit_out gets the split count the configuration used.
+static ulisse_status time_kmv_config(ulisse_ctx* ctx, int nl, int width, int tm, int nsplit,
+                                     int reps, float* ms_out, int* nsplit_out) {
+  if ((int)ctx->tune.size() < nl) ctx->tune.resize((size_t)nl, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f});
+  const ulisse_ctx::KmvTune saved = ctx->tune[nl - 1];
+  ctx->tune[nl - 1] = ulisse_ctx::KmvTune{width, tm, nsplit, 0.f, 0.f};
+  ctx->planning = true;
+  ulisse_status r = run_kmv(ctx, ctx->D, ctx->iota, nl, ctx->KD, ctx->iota, kModeK, -1);
+  ctx->planning = false;
+  if (nsplit_out) *nsplit_out = ctx->last_nsplit;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (r == ULISSE_OK && (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess))
+    r = fail(ctx, ULISSE_ERR_CUDA, "cudaEventCreate failed");
+  const long long l0 = ctx->launches;
+  const double e0 = ctx->entry_rhs;
+  std::vector<float> t;
+  if (r == ULISSE_OK) r = run_kmv(ctx, ctx->D, ctx->iota, nl, ctx->KD, ctx->iota, kModeK, -1);
+  for (int k = 0; k < reps && r == ULISSE_OK; ++k) {
+    cudaEventRecord(a, ctx->stream);
+    r = run_kmv(ctx, ctx->D, ctx->iota, nl, ctx->KD, ctx->iota, kModeK, -1);
+    cudaEventRecord(b, ctx->stream);
+    float ms = 0.f;
+    if (r == ULISSE_OK && (cudaEventSynchronize(b) != cudaSuccess ||
+                           cudaEventElapsedTime(&ms, a, b) != cudaSuccess))
+      r = fail(ctx, ULISSE_ERR_CUDA, "event timing failed");
+    t.push_back(ms);
+  }
+  ctx->launches = l0;      // tuning launches are not part of the method's work
+  ctx->entry_rhs = e0;
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  ctx->tune[nl - 1] = saved;
+  if (r != ULISSE_OK) return r;
+  std::sort(t.begin(), t.end());
+  *ms_out = t[t.size() / 2];
+  return ULISSE_OK;
+}
+
+ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, int reps,
+                              ulisse_tune_entry* out) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
+  if (max_cols < 1 || max_cols > kMaxRChunk || reps < 1 || reps > 100)
+    return fail(ctx, ULISSE_ERR_ARG, "max_cols must be 1..32 and reps 1..100");
+  if (ctx->f64) return fail(ctx, ULISSE_ERR_ARG, "the autotuner covers the FP32 and mixed paths");
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  CKS(ensure_columns(ctx, max_cols, max_cols));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  ctx->tune.assign((size_t)max_cols, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f});
+  std::vector<ulisse_ctx::KmvTune> table((size_t)max_cols);
+  ulisse_status r = ULISSE_OK;
+  for (int nl = 1; nl <= max_cols && r == ULISSE_OK; ++nl) {
+    // the default configuration first (what the launch plan picks untuned)
+    float ms_def = 0.f;
+    int split_def = 1;
+    r = time_kmv_config(ctx, nl, 0, 0, 0, reps, &ms_def, &split_def);
+    if (r != ULISSE_OK) break;
+    ulisse_ctx::KmvTune best{0, 0, 0, ms_def, ms_def};
+    // candidates: the compiled width (tensor cores: the MMA N; SIMT: the smallest
+    // instantiation >= nl, or a larger one), rows per thread (SIMT), then the j split
+    std::vector<int> widths, tms;
+    if (ctx->mixed) {
+      for (int wd : {16, 32, 64})
+        if (wd >= nl) widths.push_back(wd);
+      tms = {0};
+    } else {
+      widths = {nl, nl + 1, nl + 4};
+      tms = {2, 4};
+    }
+    for (int wd : widths) {
+      for (int tm : tms) {
+        float ms = 0.f;
+        int sp = 1;
+        r = time_kmv_config(ctx, nl, wd, tm, 0, reps, &ms, &sp);
+        if (r != ULISSE_OK) break;
+        if (ms < best.ms) best = ulisse_ctx::KmvTune{wd, tm, 0, ms, ms_def};
+      }
+      if (r != ULISSE_OK) break;
+    }
+    if (r != ULISSE_OK) break;
+    const int wd = best.width > 0 ? best.width : nl;
+    float ms_base = 0.f;
+    int base = 1;
+    r = time_kmv_config(ctx, nl, wd, best.tm, 0, 1, &ms_base, &base);   // its planned split
+    for (int sp : {base / 2, base * 2}) {
+      if (r != ULISSE_OK || sp < 1 || sp == base) continue;
+      float ms = 0.f;
+      int used = sp;
+      r = time_kmv_config(ctx, nl, wd, best.tm, sp, reps, &ms, &used);
+      if (r == ULISSE_OK && ms < best.ms) best = ulisse_ctx::KmvTune{wd, best.tm, sp, ms, ms_def};
+    }
+    if (r != ULISSE_OK) break;
+    if (best.width == 0) best.width = nl;
+    if (best.tm == 0) best.tm = ctx->cfg.kmv_rows_per_thread;
+    table[nl - 1] = best;
+  }
+  ctx->prof = prof;
+  if (r != ULISSE_OK) {
+    ctx->tune.clear();
+    return r;
+  }
+  ctx->tune = table;
+  ctx->graph_key = -1;   // a captured step graph holds the old configuration
+  if (out)
+    for (int nl = 1; nl <= max_cols; ++nl) {
+      const ulisse_ctx::KmvTune& t = table[nl - 1];
+      out[nl - 1] = ulisse_tune_entry{nl, t.width, t.tm, t.nsplit, t.ms, t.ms_default};
+    }
+  CK(cudaStreamSynchronize(ctx->stream));
+  return ULISSE_OK;
 }
 
 ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,

@@ -282,4 +282,16 @@ inline KmvPlan plan_split(long long n, int BM, int R, int elem, int slots) {
   return p;
 }
 
+// The same plan with the split count given (a tuned choice), clamped to 1..min(64, tiles).
+inline KmvPlan plan_split_forced(long long n, int BM, int R, int elem, int nsplit) {
+  KmvPlan p;
+  p.ntiles = (int)((n + kBN - 1) / kBN);
+  p.n_rb = (int)((n + BM - 1) / BM);
+  const int s = max(1, min(nsplit, min(p.ntiles, 64)));
+  p.tiles_per_split = (p.ntiles + s - 1) / s;
+  p.nsplit = (p.ntiles + p.tiles_per_split - 1) / p.tiles_per_split;
+  p.partial_bytes = p.nsplit > 1 ? (size_t)p.n_rb * p.nsplit * R * BM * elem : 0;
+  return p;
+}
+
 }  // namespace ulisse

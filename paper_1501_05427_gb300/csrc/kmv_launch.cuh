@@ -33,6 +33,7 @@ struct KmvInst {
     return occ;
   }
   static KmvPlan plan(const KmvLaunch& L) {
+    if (L.nsplit > 0) return plan_split_forced(L.n, BM, R, (int)sizeof(T), L.nsplit);
     return plan_split(L.n, BM, R, (int)sizeof(T), L.num_sms * occupancy());
   }
   static cudaError_t launch(KmvLaunch& L, cudaStream_t s) {
@@ -42,6 +43,7 @@ struct KmvInst {
       p.tiles_per_split = 0;
       p.partial_bytes = 0;
     }
+    L.planned_nsplit = p.nsplit;
     if (L.plan_only) {
       L.need_partials_bytes = p.partial_bytes;
       L.need_counters = p.nsplit > 1 ? p.n_rb : 0;
@@ -85,7 +87,8 @@ struct RList {};
 
 template <typename T, int DP, int TM, int MODE, int R0, int... Rs>
 cudaError_t dispatch_r(KmvLaunch& L, cudaStream_t s, RList<R0, Rs...>) {
-  if (L.R <= R0 || sizeof...(Rs) == 0) return KmvInst<T, DP, R0, TM, MODE>::launch(L, s);
+  if ((L.R <= R0 && L.r_min <= R0) || sizeof...(Rs) == 0)
+    return KmvInst<T, DP, R0, TM, MODE>::launch(L, s);
   if constexpr (sizeof...(Rs) > 0) return dispatch_r<T, DP, TM, MODE>(L, s, RList<Rs...>{});
   return cudaErrorInvalidValue;
 }

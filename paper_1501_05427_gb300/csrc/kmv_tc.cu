@@ -370,8 +370,10 @@ struct TcInst {
     return occ;
   }
   static cudaError_t launch(TcLaunch& L, cudaStream_t s) {
-    KmvPlan p = plan_split(L.n, kTcBM, N, 4, L.num_sms * occupancy());
+    KmvPlan p = L.nsplit > 0 ? plan_split_forced(L.n, kTcBM, N, 4, L.nsplit)
+                             : plan_split(L.n, kTcBM, N, 4, L.num_sms * occupancy());
     const size_t pbytes = p.nsplit > 1 ? (size_t)p.n_rb * p.nsplit * N * kTcBM * 4 : 0;
+    L.planned_nsplit = p.nsplit;
     if (L.plan_only) {
       L.need_partials_bytes = pbytes;
       L.need_counters = p.nsplit > 1 ? p.n_rb : 0;
@@ -420,9 +422,10 @@ struct TcInst {
 
 template <int DP>
 static cudaError_t tc_dispatch_n(TcLaunch& L, cudaStream_t s) {
-  if (L.R <= 16) return TcInst<DP, 16>::launch(L, s);
-  if (L.R <= 32) return TcInst<DP, 32>::launch(L, s);
-  if (L.R <= 64) return TcInst<DP, 64>::launch(L, s);
+  const int r = std::max(L.R, L.n_min);
+  if (r <= 16) return TcInst<DP, 16>::launch(L, s);
+  if (r <= 32) return TcInst<DP, 32>::launch(L, s);
+  if (r <= 64) return TcInst<DP, 64>::launch(L, s);
   return cudaErrorInvalidValue;
 }
 

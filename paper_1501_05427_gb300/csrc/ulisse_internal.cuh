@@ -204,6 +204,9 @@ struct KmvLaunch {
   int mode;              // KmvMode
   int which;             // dimension for kModeDLen
   int tm;                // rows per thread for K (0 = default)
+  int r_min;             // compiled column count at least this (0: the smallest >= R)
+  int nsplit;            // j-range split count (0: the launch plan's choice)
+  int planned_nsplit;    // out: the split count used (or planned)
   void* partials;        // split-j scratch
   size_t partials_bytes;
   int* counters;         // one per row block, zero between launches
@@ -255,6 +258,9 @@ struct TcLaunch {
   long long n;
   int DP;
   const DevParams* params;
+  int n_min;             // MMA N at least this (0: the smallest of 16, 32, 64 >= R)
+  int nsplit;            // j-range split count (0: the launch plan's choice)
+  int planned_nsplit;    // out: the split count used (or planned)
   void* partials;
   size_t partials_bytes;
   int* counters;

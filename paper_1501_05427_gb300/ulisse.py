@@ -34,7 +34,7 @@ EXPORTED = [
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
-    "ulisse_set_graph",
+    "ulisse_set_graph", "ulisse_autotune",
 ]
 
 
@@ -76,6 +76,12 @@ class ulisse_ws_state(ctypes.Structure):
                 ("pair_rows", ctypes.c_void_p), ("mu", ctypes.c_void_p), ("sd", ctypes.c_void_p),
                 ("pair_psi", ctypes.c_void_p), ("n_pairs", ctypes.c_int),
                 ("n_params", ctypes.c_longlong)]
+
+
+class ulisse_tune_entry(ctypes.Structure):
+    _fields_ = [("live_cols", ctypes.c_int), ("width", ctypes.c_int),
+                ("rows_per_thread", ctypes.c_int), ("nsplit", ctypes.c_int),
+                ("ms", ctypes.c_float), ("ms_default", ctypes.c_float)]
 
 
 class UlisseError(RuntimeError):
@@ -127,6 +133,7 @@ def load():
     lib.ulisse_batch_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_batch_sgld_step.argtypes = [P, P, D, U64, P]
     lib.ulisse_set_graph.argtypes = [P, I]
+    lib.ulisse_autotune.argtypes = [P, P, I, I, ctypes.POINTER(ulisse_tune_entry)]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -327,6 +334,15 @@ class Context:
         self._check(self._lib.ulisse_ws_x0(self._h, _hptr(psi), int(bool(bf16)),
                                            ctypes.c_void_p(x0.data_ptr())))
         return x0
+
+    def autotune(self, psi, max_cols=None, reps=3):
+        """Tune the K V launch configuration for 1..max_cols live columns; returns the table
+        as a list of dicts."""
+        max_cols = max_cols or (1 + self.cfg.n_probes)
+        out = (ulisse_tune_entry * max_cols)()
+        psi = _f64_host(psi, self.p)
+        self._check(self._lib.ulisse_autotune(self._h, _hptr(psi), max_cols, reps, out))
+        return [{k: getattr(e, k) for k, _ in ulisse_tune_entry._fields_} for e in out]
 
     def set_graph(self, enable=True):
         """sgld_chain: one CUDA-graph launch per step (True) or the host loop (False)."""
@@ -549,3 +565,7 @@ def ulisse_batch_sgld_step(ctx: BatchContext, psi, eps_t, step):
 
 def ulisse_set_graph(ctx: Context, enable=True):
     ctx.set_graph(enable)
+
+
+def ulisse_autotune(ctx: Context, psi, max_cols=None, reps=3):
+    return ctx.autotune(psi, max_cols, reps)
