@@ -326,8 +326,8 @@ ulisse_status ulisse_ws_x0(ulisse_ctx *ctx, const double *psi, int bf16, float *
  * sweep; the work list has one item per (problem, 256-row block), longest rows first.
  * Parameters and gradients are packed: problem b's p_b values follow problem b-1's.
  * Batched contexts run the FP32 path (cfg->precision must be ULISSE_PREC_FP32), take
- * n_probes <= 16, and accept only the ulisse_batch_* calls (plus counters and destroy);
- * the single-problem calls return ULISSE_ERR_ARG on them.
+ * n_probes <= 16, and accept only the ulisse_batch_* calls (plus ulisse_set_graph,
+ * counters and destroy); the single-problem calls return ULISSE_ERR_ARG on them.
  *
  *   n_problems  1 .. 4096.   n, d: host arrays of n_problems sizes (1 <= d_b <= 8).
  *   X, y        host arrays of n_problems DEVICE pointers (row-major n_b x d_b, and n_b);
@@ -356,6 +356,19 @@ ulisse_status ulisse_batch_grad(ulisse_ctx *ctx, const double *psi, unsigned lon
  *   psi_inout host, packed; g_out NULL or host, packed. */
 ulisse_status ulisse_batch_sgld_step(ulisse_ctx *ctx, double *psi_inout, double eps_t,
                                      unsigned long long step, double *g_out);
+
+/* n_steps SGLD steps of every problem with the packed parameters resident on the device.
+ *   psi_dev   device, packed parameters (in place).
+ *   eps_dev   device, n_steps step sizes.   step0: step number of the first step.
+ *   trace_dev device, NULL or n_steps x n_params (packed parameters after each step).
+ * With the graph enabled (ulisse_set_graph, the default) each step is ONE launch of a CUDA
+ * graph holding the whole batched step: every problem's prescale, probes and CG start, the
+ * round loop as a conditional WHILE node (one batched compaction, the persistent K V over
+ * all live columns of all problems with its compiled width chosen by a SWITCH node, three
+ * batched CG launches), the persistent gradient sweep and the updates.  The host loop runs
+ * the same launches and gives the same results. */
+ulisse_status ulisse_batch_sgld_chain(ulisse_ctx *ctx, double *psi_dev, const double *eps_dev,
+                                      int n_steps, unsigned long long step0, double *trace_dev);
 
 /* ulisse_sgld_chain runs each step as ONE launch of a CUDA graph (enable != 0, the default)
  * or from the host loop (0).  The graph holds the whole step: prescale, probes, the CG +

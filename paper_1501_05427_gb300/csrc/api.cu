@@ -120,6 +120,13 @@ struct ulisse_ctx {
   int* b_h_status = nullptr;       // pinned, one status word per problem
   double* b_gpart = nullptr;       // n_items x kMaxP
   double* b_g = nullptr;           // problems x kMaxP
+  CgArgs<float>* b_cgargs = nullptr;   // device, one per problem (batched CG launches)
+  BatchCgProb* b_cgprob = nullptr;     // device, one per problem (batched compaction)
+  int* b_rmax = nullptr;           // device: largest live count of the round
+  int* b_h_rmax = nullptr;         // pinned
+  double* b_psi = nullptr;         // device: packed parameters of all problems
+  int b_np = 0;                    // packed parameter count
+  int b_maxch = 1;                 // largest chunk count of the batched CG launches
 
   // event timing of the O(n^2) kernels (ulisse_profile_enable)
   bool prof = false;
@@ -1280,7 +1287,6 @@ static void graph_fold_counters(ulisse_ctx* ctx, int n_steps) {
 
 ulisse_status ulisse_set_graph(ulisse_ctx* ctx, int enable) {
   if (!ctx) return ULISSE_ERR_ARG;
-  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: use the ulisse_batch_* calls");
   ctx->graph_enabled = enable != 0;
   return ULISSE_OK;
 }
@@ -1766,6 +1772,7 @@ ulisse_status ulisse_batch_kmv(ulisse_ctx* ctx, const double* psi, const float* 
     if (!V[b] || !U[b]) return fail(ctx, ULISSE_ERR_ARG, "V[b] or U[b] is null");
   CKS(batch_set_psi(ctx, psi));
   CKS(batch_clear_status(ctx));
+  graph_release(ctx);   // the products below may reallocate the problems' buffers
   std::vector<BatchKmvDesc> desc(B);
   std::vector<int> rc(B, R);
   double entries = 0.0;
@@ -1799,105 +1806,304 @@ ulisse_status ulisse_batch_kmv(ulisse_ctx* ctx, const double* psi, const float* 
   return status_to_result(ctx, st);
 }
 
-// The gradient path of every problem for one step (psi already on each sub-context): per
-// problem the prologue (prescale, probes, metadata), CG + ULISSE in lock-step rounds with
-// one persistent K V launch per round over all live columns of all problems, then one
-// persistent gradient launch.  The gradients land in b_g (kMaxP doubles per problem).
-static ulisse_status batch_grad_core(ulisse_ctx* ctx, unsigned long long step) {
+// Streams and counting flags of a batch and all its problems (capture redirects both).
+static void batch_set_stream(ulisse_ctx* ctx, cudaStream_t s, bool capturing) {
+  ctx->stream = s;
+  ctx->capturing = capturing;
+  for (ulisse_ctx* sub : ctx->subs) {
+    sub->stream = s;
+    sub->capturing = capturing;
+  }
+}
+
+// Host-side preparation of a batched step (idempotent): every problem's buffers, gradient
+// maps, column metadata, identity M and zero prior; the descriptor arrays of the batched
+// launches; the chain slot.  Nothing here may run inside a capture.
+static ulisse_status batch_prepare(ulisse_ctx* ctx) {
   const int B = (int)ctx->subs.size();
   const int nr = ctx->cfg.n_probes, R = 1 + nr;
-  std::vector<CgArgs<float>> args(B);
-  for (int b = 0; b < B; ++b) {
-    ulisse_ctx* sub = ctx->subs[b];
-    SUBS(ctx, sub, grad_core(sub, step, true));
-    args[b] = cg_args<float>(sub, 0, step);
-    cg_init_kernel<float><<<R, kCgNT, 0, ctx->stream>>>(args[b]);
-    CK(cudaGetLastError());
+  for (ulisse_ctx* sub : ctx->subs) {
+    SUBS(ctx, sub, ensure_columns(sub, R, R + 1));
+    SUBS(ctx, sub, ensure_grad_maps(sub, nr));
+    if (sub->meta_grad_R != R) {
+      std::vector<int> n_est(R, 1);
+      n_est[0] = 2;
+      int tot = 0;
+      SUBS(ctx, sub, upload_meta(sub, R, n_est.data(), &tot));
+      sub->meta_grad_R = R;
+    }
+    const int p = sub->d + 2;
+    if (!sub->m_identity) {
+      std::vector<double> I((size_t)p * p, 0.0);
+      for (int i = 0; i < p; ++i) I[(size_t)i * p + i] = 1.0;
+      CK(cudaMemcpyAsync(sub->M_dev, I.data(), sizeof(double) * p * p, cudaMemcpyHostToDevice,
+                         ctx->stream));
+      sub->m_identity = true;
+    }
+    if (!sub->prior_zero) {
+      CK(cudaMemsetAsync(sub->prior_dev, 0, sizeof(double) * p, ctx->stream));
+      sub->prior_zero = true;
+    }
   }
-  ctx->launches += B;
+  if (!ctx->b_cgargs) {
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_cgargs), sizeof(CgArgs<float>) * B));
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_cgprob), sizeof(BatchCgProb) * B));
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_rmax), sizeof(int)));
+    int np = 0;
+    for (ulisse_ctx* sub : ctx->subs) np += sub->d + 2;
+    ctx->b_np = np;
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_psi), sizeof(double) * np));
+    if (cudaMallocHost(&ctx->b_h_rmax, sizeof(int)) != cudaSuccess)
+      return fail(ctx, ULISSE_ERR_NOMEM, "cudaMallocHost failed");
+    prime_kmv_batch();
+    prime_grad_batch();
+  }
+  CKS(graph_alloc(ctx));
+  std::vector<CgArgs<float>> args(B);
+  std::vector<BatchCgProb> probs(B);
   std::vector<BatchKmvDesc> kd(B);
+  std::vector<BatchGradDesc> gd(B);
+  int slot0 = 0, maxch = 1;
   for (int b = 0; b < B; ++b) {
     ulisse_ctx* sub = ctx->subs[b];
+    CgArgs<float> a = cg_args<float>(sub, 0, 0);
+    a.cs = ctx->chain;
+    // 4096 rows per CTA, more when the problem would need over kMaxCgChunks chunks
+    a.chunk = std::max<long long>(kBatchCgChunk,
+                                  ((sub->n + kMaxCgChunks - 1) / kMaxCgChunks + 255) / 256 * 256);
+    a.nchunk = (int)((sub->n + a.chunk - 1) / a.chunk);
+    a.n_live = sub->n_live_dev;
+    maxch = std::max(maxch, a.nchunk);
+    args[b] = a;
+    probs[b] = BatchCgProb{sub->st, sub->st_next, sub->live, sub->n_live_dev, R, sub->n};
     kd[b] = BatchKmvDesc{(const float*)sub->xhat, sub->n, sub->DP, 0, sub->params,
                          (const float*)sub->D, sub->ldn, sub->live, (float*)sub->KD, sub->ldn,
-                         sub->live, ctx->b_nlive + b};
-  }
-  CK(cudaMemcpyAsync(ctx->b_kdesc, kd.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
-                     ctx->stream));
-  std::vector<int> n_prev(B, 0);
-  std::vector<char> active(B, 1);
-  for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
-    for (int b = 0; b < B; ++b) {
-      if (!active[b]) continue;
-      ulisse_ctx* sub = ctx->subs[b];
-      compact_kernel<<<1, 32, 0, ctx->stream>>>(sub->st, sub->st_next, R, n_prev[b], sub->live,
-                                                ctx->b_nlive + b);
-    }
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(ctx->b_h_nlive, ctx->b_nlive, sizeof(int) * B, cudaMemcpyDeviceToHost,
-                       ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
-    int rmax = 0, n_active = 0;
-    double entries = 0.0;
-    for (int b = 0; b < B; ++b) {
-      if (!active[b]) continue;
-      ++n_active;
-      const int nl = ctx->b_h_nlive[b];
-      rmax = std::max(rmax, nl);
-      entries += (double)ctx->subs[b]->n * (double)ctx->subs[b]->n * nl;
-    }
-    ctx->launches += n_active;
-    if (rmax == 0) break;
-    CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue, rmax,
-                        ctx->num_sms, ctx->status_dev, ctx->stream));
-    ctx->launches++;
-    ctx->mvp_rounds++;
-    ctx->entry_rhs += entries;
-    for (int b = 0; b < B; ++b) {
-      if (!active[b]) continue;
-      const int nl = ctx->b_h_nlive[b];
-      n_prev[b] = nl;
-      if (nl == 0) {
-        active[b] = 0;
-        continue;
-      }
-      ulisse_ctx* sub = ctx->subs[b];
-      CgArgs<float>& a = args[b];
-      // about two CTAs per SM over all of this problem's live columns, >= 2048 rows each
-      const long long target = std::max(1, (2 * ctx->num_sms + nl - 1) / nl);
-      long long ch = std::max<long long>((sub->n + target - 1) / target, 2048);
-      ch = std::max<long long>(ch, (sub->n + kMaxCgChunks - 1) / kMaxCgChunks);
-      ch = (ch + 255) / 256 * 256;
-      a.chunk = ch;
-      a.nchunk = (int)((sub->n + ch - 1) / ch);
-      const dim3 grid(a.nchunk, nl);
-      cg_dot_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
-      cg_update_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
-      cg_finish_kernel<float><<<grid, kCgChunkNT, 0, ctx->stream>>>(a);
-      ctx->launches += 3;
-    }
-    CK(cudaGetLastError());
-  }
-  // a2 (second estimate of K^{-1} y) becomes the right factor of the quadratic term.
-  std::vector<BatchGradDesc> gd(B);
-  int slot0 = 0;
-  for (int b = 0; b < B; ++b) {
-    ulisse_ctx* sub = ctx->subs[b];
-    CK(cudaMemcpyAsync(sub->B, (char*)sub->SE + sub->ldn * 4, sub->ldn * 4,
-                       cudaMemcpyDeviceToDevice, ctx->stream));
+                         sub->live, sub->n_live_dev};
     const int nslots = (int)((sub->n + kBatchBM - 1) / kBatchBM);
     gd[b] = BatchGradDesc{(const float*)sub->xhat, sub->n, sub->DP, sub->d, sub->params,
                           (const float*)sub->SE, sub->amap, (const float*)sub->sa_dev,
                           (const float*)sub->B, sub->bmap, sub->ldn, R, slot0, nslots, 0,
                           ctx->b_g + (long long)b * kMaxP};
     slot0 += nslots;
-    ctx->entry_rhs += (double)sub->n * (double)sub->n * R;
   }
+  ctx->b_maxch = maxch;
+  CK(cudaMemcpyAsync(ctx->b_cgargs, args.data(), sizeof(CgArgs<float>) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_cgprob, probs.data(), sizeof(BatchCgProb) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_kdesc, kd.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_gdesc, gd.data(), sizeof(BatchGradDesc) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
+  return ULISSE_OK;
+}
+
+// One batched step on ctx->stream: per problem its parameters from the packed vector, the
+// prescale, y and the probes, the CG start; then CG + ULISSE in lock-step rounds (one
+// batched compaction, one persistent K V over all live columns of all problems, three
+// batched CG launches per round); then the persistent gradient sweep and, with sgld, every
+// problem's update and the packed parameters back.  The host loop and the step graph run
+// exactly these launches; in the graph the round loop is a WHILE node whose compaction sets
+// the loop condition and a SWITCH over the K V width.
+static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) {
+  const int B = (int)ctx->subs.size();
+  const int nr = ctx->cfg.n_probes, R = 1 + nr;
+  int off = 0;
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    const int p = sub->d + 2;
+    CK(cudaMemcpyAsync(sub->psi_dev, ctx->b_psi + off, sizeof(double) * p,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
+    off += p;
+    SUBS(ctx, sub, prescale(sub));
+    CK(cudaMemcpyAsync(sub->B, sub->y, sub->ldn * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    dim3 pg((unsigned)std::min<long long>((sub->n + 255) / 256, 2LL * ctx->num_sms), nr);
+    probes_kernel<float><<<pg, 256, 0, ctx->stream>>>((float*)sub->B, sub->ldn, sub->n, nr,
+                                                      ctx->cfg.probe_kind, sub->cfg.seed, 0,
+                                                      ctx->chain, ctx->cfg.probe_refresh);
+    CgArgs<float> a = cg_args<float>(sub, 0, 0);
+    a.cs = ctx->chain;
+    cg_init_kernel<float><<<R, kCgNT, 0, ctx->stream>>>(a);
+    CK(cudaMemsetAsync(sub->n_live_dev, 0, sizeof(int), ctx->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemsetAsync(ctx->gstat + 3, 0, sizeof(long long), ctx->stream));
+  const dim3 cg_grid(ctx->b_maxch, R, B);
+  auto cg_round = [&](cudaStream_t s) {
+    cg_dot_batch_kernel<float><<<cg_grid, kCgChunkNT, 0, s>>>(ctx->b_cgargs);
+    cg_update_batch_kernel<float><<<cg_grid, kCgChunkNT, 0, s>>>(ctx->b_cgargs);
+    cg_finish_batch_kernel<float><<<cg_grid, kCgChunkNT, 0, s>>>(ctx->b_cgargs);
+    return cudaGetLastError();
+  };
+  const int max_rounds = ctx->cfg.max_iter + 2;
+  if (!in_graph) {
+    for (int it = 0; it < max_rounds + 1; ++it) {
+      compact_batch_kernel<<<1, 256, 0, ctx->stream>>>(ctx->b_cgprob, B, ctx->b_rmax, 0, 0, 0,
+                                                       max_rounds, ctx->gstat, ctx->status_dev);
+      CK(cudaGetLastError());
+      CK(cudaMemcpyAsync(ctx->b_h_rmax, ctx->b_rmax, sizeof(int), cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      const int rmax = *ctx->b_h_rmax;
+      if (rmax == 0) break;
+      CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue,
+                          kBatchWidths[batch_width_bucket(rmax)], ctx->num_sms, ctx->status_dev,
+                          ctx->stream));
+      CK(cg_round(ctx->stream));
+    }
+  } else {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(ctx->stream, &cst, nullptr, &g, &deps, nullptr, &ndeps));
+    cudaGraphConditionalHandle h_loop, h_branch;
+    CK(cudaGraphConditionalHandleCreate(&h_loop, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = h_loop;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, g, deps, nullptr, ndeps, &wp));
+    CK(cudaStreamUpdateCaptureDependencies(ctx->stream, &wnode, nullptr, 1,
+                                           cudaStreamSetCaptureDependencies));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    CK(cudaGraphConditionalHandleCreate(&h_branch, body, 5, cudaGraphCondAssignDefault));
+    cudaStream_t s2 = ctx->cap_stream2;
+    CK(cudaStreamBeginCaptureToGraph(s2, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeThreadLocal));
+    compact_batch_kernel<<<1, 256, 0, s2>>>(ctx->b_cgprob, B, ctx->b_rmax, 1, h_loop, h_branch,
+                                            max_rounds, ctx->gstat, ctx->status_dev);
+    cudaError_t e = cudaGetLastError();
+    const cudaGraphNode_t* bdeps = nullptr;
+    size_t nbdeps = 0;
+    cudaGraph_t bg = nullptr;
+    if (e == cudaSuccess)
+      e = cudaStreamGetCaptureInfo(s2, &cst, nullptr, &bg, &bdeps, nullptr, &nbdeps);
+    cudaGraphNodeParams sp = {};
+    sp.type = cudaGraphNodeTypeConditional;
+    sp.conditional.handle = h_branch;
+    sp.conditional.type = cudaGraphCondTypeSwitch;
+    sp.conditional.size = 5;
+    cudaGraphNode_t snode;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&snode, bg, bdeps, nullptr, nbdeps, &sp);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(s2, &snode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) e = cg_round(s2);
+    cudaGraph_t tmp = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(s2, &tmp);
+    CK(e);
+    CK(e2);
+    for (int k = 0; k < 5; ++k) {
+      CK(cudaStreamBeginCaptureToGraph(s2, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
+                                       cudaStreamCaptureModeThreadLocal));
+      const cudaError_t e3 = launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items,
+                                              ctx->b_queue, kBatchWidths[k], ctx->num_sms,
+                                              ctx->status_dev, s2);
+      const cudaError_t e4 = cudaStreamEndCapture(s2, &tmp);
+      CK(e3);
+      CK(e4);
+    }
+  }
+  // the second estimate of K^{-1} y as the right factor; the gradient sweep
+  for (ulisse_ctx* sub : ctx->subs)
+    CK(cudaMemcpyAsync(sub->B, (char*)sub->SE + sub->ldn * 4, sub->ldn * 4,
+                       cudaMemcpyDeviceToDevice, ctx->stream));
   CK(launch_grad_batch(ctx->b_gdesc, B, ctx->b_items, ctx->b_n_items, ctx->b_queue, ctx->b_gpart,
                        R, ctx->num_sms, ctx->status_dev, ctx->stream));
-  ctx->launches += 2;
+  if (sgld) {
+    off = 0;
+    for (int b = 0; b < B; ++b) {
+      ulisse_ctx* sub = ctx->subs[b];
+      const int p = sub->d + 2;
+      sgld_chain_kernel<<<1, 32, 0, ctx->stream>>>(sub->psi_dev, ctx->b_g + (long long)b * kMaxP,
+                                                   sub->M_dev, sub->prior_dev, p, sub->cfg.seed,
+                                                   ctx->chain, sub->status_dev, 0, ctx->b_np, off);
+      off += p;
+    }
+    chain_advance_kernel<<<1, 32, 0, ctx->stream>>>(ctx->chain);
+    CK(cudaGetLastError());
+    off = 0;
+    for (int b = 0; b < B; ++b) {
+      ulisse_ctx* sub = ctx->subs[b];
+      const int p = sub->d + 2;
+      CK(cudaMemcpyAsync(ctx->b_psi + off, sub->psi_dev, sizeof(double) * p,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+      off += p;
+    }
+  }
+  return ULISSE_OK;
+}
+
+// Work of one batched step outside the round loop (the loop's share is counted on the device).
+static void batch_count_fixed(ulisse_ctx* ctx, int steps, bool sgld) {
+  const int B = (int)ctx->subs.size();
+  const int R = 1 + ctx->cfg.n_probes;
+  double ent = 0.0;
+  for (ulisse_ctx* sub : ctx->subs) ent += (double)sub->n * (double)sub->n * R;
+  ctx->launches += (long long)steps * (3LL * B + 2 + (sgld ? B + 1 : 0));
+  ctx->entry_rhs += steps * ent;
+}
+
+static ulisse_status batch_fold_gstat(ulisse_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->h_gstat, ctx->gstat, sizeof(long long) * 4, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->mvp_rounds += ctx->h_gstat[0];
+  ctx->entry_rhs += (double)ctx->h_gstat[1];
+  ctx->launches += ctx->h_gstat[2];
+  CK(cudaMemsetAsync(ctx->gstat, 0, sizeof(long long) * 3, ctx->stream));
+  return ULISSE_OK;
+}
+
+static ulisse_status batch_graph_build(ulisse_ctx* ctx) {
+  graph_release(ctx);
+  if (!ctx->cap_stream) {
+    CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->cap_stream2, cudaStreamNonBlocking));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  cudaStream_t saved = ctx->stream;
+  batch_set_stream(ctx, ctx->cap_stream, true);
+  ulisse_status r = ULISSE_OK;
+  cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) r = batch_step_body(ctx, true, true);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(ctx->cap_stream, &graph) : e;
+  batch_set_stream(ctx, saved, false);
+  if (r != ULISSE_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(ctx, ULISSE_ERR_CUDA, std::string("batched step graph capture: ") + cudaGetErrorString(e2));
+  }
+  ctx->step_graph = graph;
+  CK(cudaGraphInstantiate(&ctx->step_exec, graph, 0));
+  ctx->graph_key = 1000;
+  return ULISSE_OK;
+}
+
+// n_steps batched SGLD steps from the packed parameters already in b_psi, with the chain
+// slot already set: one graph launch per step, or the host loop.
+static ulisse_status batch_run_steps(ulisse_ctx* ctx, int n_steps) {
+  if (ctx->graph_enabled) {
+    if (ctx->graph_key != 1000) CKS(batch_graph_build(ctx));
+    for (int k = 0; k < n_steps; ++k) CK(cudaGraphLaunch(ctx->step_exec, ctx->stream));
+  } else {
+    for (int k = 0; k < n_steps; ++k) CKS(batch_step_body(ctx, true, false));
+  }
+  batch_count_fixed(ctx, n_steps, true);
+  return ULISSE_OK;
+}
+
+static ulisse_status batch_set_chain(ulisse_ctx* ctx, unsigned long long step0,
+                                     const double* eps_dev, double* trace_dev) {
+  const ChainSlot cs{0, step0, eps_dev, trace_dev};
+  CK(cudaMemcpyAsync(ctx->chain, &cs, sizeof(ChainSlot), cudaMemcpyHostToDevice, ctx->stream));
   return ULISSE_OK;
 }
 
@@ -1907,11 +2113,17 @@ ulisse_status ulisse_batch_grad(ulisse_ctx* ctx, const double* psi, unsigned lon
   if (!g) return fail(ctx, ULISSE_ERR_ARG, "g is null");
   CKS(batch_set_psi(ctx, psi));
   CKS(batch_clear_status(ctx));
-  CKS(batch_grad_core(ctx, step));
+  CKS(batch_prepare(ctx));
+  CK(cudaMemcpyAsync(ctx->b_psi, psi, sizeof(double) * ctx->b_np, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CKS(batch_set_chain(ctx, step, ctx->eps_one, nullptr));
+  CKS(batch_step_body(ctx, false, false));
+  batch_count_fixed(ctx, 1, false);
   const int B = (int)ctx->subs.size();
   std::vector<double> gall((size_t)B * kMaxP);
   CK(cudaMemcpyAsync(gall.data(), ctx->b_g, sizeof(double) * gall.size(), cudaMemcpyDeviceToHost,
                      ctx->stream));
+  CKS(batch_fold_gstat(ctx));
   int st = 0;
   CKS(batch_read_status(ctx, &st));
   for (int b = 0; b < B; ++b)
@@ -1929,30 +2141,49 @@ ulisse_status ulisse_batch_sgld_step(ulisse_ctx* ctx, double* psi_inout, double 
   if (!(eps_t >= 0.0) || !std::isfinite(eps_t)) return fail(ctx, ULISSE_ERR_ARG, "eps_t invalid");
   CKS(batch_set_psi(ctx, psi_inout));
   CKS(batch_clear_status(ctx));
-  CKS(batch_grad_core(ctx, step));
-  const int B = (int)ctx->subs.size();
-  for (int b = 0; b < B; ++b) {
-    ulisse_ctx* sub = ctx->subs[b];
-    sgld_kernel<<<1, 32, 0, ctx->stream>>>(sub->psi_dev, ctx->b_g + (long long)b * kMaxP, nullptr,
-                                           nullptr, nullptr, eps_t, sub->d + 2, sub->cfg.seed,
-                                           step, nullptr, sub->status_dev);
-  }
-  CK(cudaGetLastError());
-  ctx->launches += B;
+  CKS(batch_prepare(ctx));
+  CK(cudaMemcpyAsync(ctx->b_psi, psi_inout, sizeof(double) * ctx->b_np, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->eps_one, &eps_t, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+  CKS(batch_set_chain(ctx, step, ctx->eps_one, nullptr));
+  CKS(batch_run_steps(ctx, 1));
+  CKS(batch_fold_gstat(ctx));
   int st = 0;
   CKS(batch_read_status(ctx, &st));
   ulisse_status r = status_to_result(ctx, st);
   if (r == ULISSE_ERR_ARG) return r;
-  for (int b = 0; b < B; ++b) {
-    ulisse_ctx* sub = ctx->subs[b];
-    CK(cudaMemcpyAsync(psi_inout + ctx->sub_p_off[b], sub->psi_dev, sizeof(double) * (sub->d + 2),
-                       cudaMemcpyDeviceToHost, ctx->stream));
-    if (g_out)
-      CK(cudaMemcpyAsync(g_out + ctx->sub_p_off[b], ctx->b_g + (long long)b * kMaxP,
-                         sizeof(double) * (sub->d + 2), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(psi_inout, ctx->b_psi, sizeof(double) * ctx->b_np, cudaMemcpyDeviceToHost,
+                     ctx->stream));
+  if (g_out) {
+    const int B = (int)ctx->subs.size();
+    std::vector<double> gall((size_t)B * kMaxP);
+    CK(cudaMemcpyAsync(gall.data(), ctx->b_g, sizeof(double) * gall.size(), cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (int b = 0; b < B; ++b)
+      for (int k = 0; k < ctx->subs[b]->d + 2; ++k)
+        g_out[ctx->sub_p_off[b] + k] = gall[(size_t)b * kMaxP + k];
   }
   CK(cudaStreamSynchronize(ctx->stream));
   return r;
+}
+
+ulisse_status ulisse_batch_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const double* eps_dev,
+                                      int n_steps, unsigned long long step0, double* trace_dev) {
+  BATCHED_ONLY(ctx);
+  if (!psi_dev || !eps_dev || n_steps < 0) return fail(ctx, ULISSE_ERR_ARG, "bad chain arguments");
+  CKS(batch_clear_status(ctx));
+  CKS(batch_prepare(ctx));
+  CK(cudaMemcpyAsync(ctx->b_psi, psi_dev, sizeof(double) * ctx->b_np, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CKS(batch_set_chain(ctx, step0, eps_dev, trace_dev));
+  CKS(batch_run_steps(ctx, n_steps));
+  CK(cudaMemcpyAsync(psi_dev, ctx->b_psi, sizeof(double) * ctx->b_np, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  CKS(batch_fold_gstat(ctx));
+  int st = 0;
+  CKS(batch_read_status(ctx, &st));
+  return status_to_result(ctx, st);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -2077,8 +2308,7 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
 ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,
                               long long* kernel_launches) {
   if (!ctx) return ULISSE_ERR_ARG;
-  long long launches = ctx->launches;
-  for (const ulisse_ctx* sub : ctx->subs) launches += sub->launches;   // batched problems
+  const long long launches = ctx->launches;
   if (mvp_rounds) *mvp_rounds = ctx->mvp_rounds;
   if (entry_rhs) *entry_rhs = ctx->entry_rhs;
   if (kernel_launches) *kernel_launches = launches;
@@ -2137,6 +2367,10 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   dev_free(reinterpret_cast<void*&>(ctx->gstat));
   dev_free(reinterpret_cast<void*&>(ctx->eps_one));
   if (ctx->h_gstat) cudaFreeHost(ctx->h_gstat);
+  for (void** p : {reinterpret_cast<void**>(&ctx->b_cgargs), reinterpret_cast<void**>(&ctx->b_cgprob),
+                   reinterpret_cast<void**>(&ctx->b_rmax), reinterpret_cast<void**>(&ctx->b_psi)})
+    dev_free(*p);
+  if (ctx->b_h_rmax) cudaFreeHost(ctx->b_h_rmax);
   for (void** p : {reinterpret_cast<void**>(&ctx->b_items), reinterpret_cast<void**>(&ctx->b_kdesc),
                    reinterpret_cast<void**>(&ctx->b_gdesc), reinterpret_cast<void**>(&ctx->b_queue),
                    reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),

@@ -63,6 +63,11 @@ struct BatchGradDesc {
 // R_max: the largest live count over the problems (selects the compiled column count).
 cudaError_t launch_kmv_batch(const BatchKmvDesc* descs, const BatchItem* items, int n_items,
                              int* queue, int R_max, int num_sms, int* status, cudaStream_t s);
+// Occupancy queries and attributes of every compiled width, made ahead of a graph capture.
+void prime_kmv_batch();
+void prime_grad_batch();
+constexpr int kBatchWidths[5] = {2, 4, 9, 17, 32};   // compiled widths of the batched K V
+constexpr long long kBatchCgChunk = 4096;          // rows per CTA of the batched CG kernels
 cudaError_t launch_grad_batch(const BatchGradDesc* descs, int n_probs, const BatchItem* items,
                               int n_items, int* queue, double* partials, int M, int num_sms,
                               int* status, cudaStream_t s);

@@ -221,25 +221,40 @@ __global__ void grad_batch_reduce_kernel(const BatchGradDesc* __restrict__ descs
 }
 
 template <int M>
-static cudaError_t grad_batch_launch(const BatchGradDesc* descs, const BatchItem* items,
-                                     int n_items, int* queue, double* partials, int num_sms,
-                                     int* status, cudaStream_t s) {
-  const size_t smem = (size_t)kStages * (kGBatchXStage + M * kBN) * sizeof(float) +
-                      kStages * sizeof(uint64_t);
+static size_t grad_batch_smem() {
+  return (size_t)kStages * (kGBatchXStage + M * kBN) * sizeof(float) + kStages * sizeof(uint64_t);
+}
+
+template <int M>
+static int grad_batch_occupancy() {
   static int occ = 1;
   static std::once_flag once;
-  std::call_once(once, [smem] {
+  std::call_once(once, [] {
     auto fn = grad_batch_kernel<M>;
-    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)grad_batch_smem<M>());
     int o = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kBatchNT, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fn, kBatchNT, grad_batch_smem<M>()) !=
+        cudaSuccess)
       o = 1;
     occ = std::max(o, 1);
   });
-  const int grid = std::max(1, std::min(n_items, num_sms * occ));
-  grad_batch_kernel<M><<<grid, kBatchNT, smem, s>>>(descs, items, n_items, queue, partials,
-                                                    status);
+  return occ;
+}
+
+template <int M>
+static cudaError_t grad_batch_launch(const BatchGradDesc* descs, const BatchItem* items,
+                                     int n_items, int* queue, double* partials, int num_sms,
+                                     int* status, cudaStream_t s) {
+  const int grid = std::max(1, std::min(n_items, num_sms * grad_batch_occupancy<M>()));
+  grad_batch_kernel<M><<<grid, kBatchNT, grad_batch_smem<M>(), s>>>(descs, items, n_items, queue,
+                                                                   partials, status);
   return cudaGetLastError();
+}
+
+void prime_grad_batch() {
+  (void)grad_batch_occupancy<5>();
+  (void)grad_batch_occupancy<9>();
+  (void)grad_batch_occupancy<17>();
 }
 
 cudaError_t launch_grad_batch(const BatchGradDesc* descs, int n_probs, const BatchItem* items,

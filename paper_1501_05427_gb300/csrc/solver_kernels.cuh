@@ -63,6 +63,7 @@ struct CgArgs {
   int has_s0;
   unsigned long long seed, step;
   const ChainSlot* cs;   // when set, the step number comes from the chain slot
+  const int* n_live;     // batched launches: this problem's live column count
   int* status;
 };
 
@@ -156,29 +157,31 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
 constexpr int kCgChunkNT = 256;
 
 template <typename T>
-__device__ inline void chunk_range(const CgArgs<T>& a, long long* i0, long long* i1) {
-  *i0 = (long long)blockIdx.x * a.chunk;
+__device__ inline void chunk_range(const CgArgs<T>& a, int ch, long long* i0, long long* i1) {
+  *i0 = (long long)ch * a.chunk;
   *i1 = min(a.n, *i0 + a.chunk);
 }
 
+// The bodies below take the chunk (ch) and the live-list index (li) of the CTA: the
+// single-problem kernels pass their grid coordinates, the batched ones add the problem.
 template <typename T>
-__global__ void __launch_bounds__(kCgChunkNT) cg_dot_kernel(const CgArgs<T> a) {
+__device__ inline void cg_dot_body(const CgArgs<T>& a, int ch, int li) {
   __shared__ double red[kCgChunkNT / 32];
-  const int c = a.live[blockIdx.y];
+  const int c = a.live[li];
   const T* d = a.D + c * a.ld;
   const T* kd = a.KD + c * a.ld;
   long long i0, i1;
-  chunk_range(a, &i0, &i1);
+  chunk_range(a, ch, &i0, &i1);
   double p = 0.0;
   for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) p += (double)d[i] * (double)kd[i];
   p = block_sum<kCgChunkNT>(p, red);
-  if (threadIdx.x == 0) a.part1[(long long)c * a.nchunk + blockIdx.x] = p;
+  if (threadIdx.x == 0) a.part1[(long long)c * a.nchunk + ch] = p;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCgChunkNT) cg_update_kernel(const CgArgs<T> a) {
+__device__ inline void cg_update_body(const CgArgs<T>& a, int ch, int li) {
   __shared__ double red[kCgChunkNT / 32];
-  const int c = a.live[blockIdx.y];
+  const int c = a.live[li];
   const ColState& st = a.st[c];
   double dKd = 0.0;
   for (int k = 0; k < a.nchunk; ++k) dKd += a.part1[(long long)c * a.nchunk + k];
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_update_kernel(const CgArgs<T> a
   T* se0 = a.SE + (long long)st.est_off * a.ld;
   T* se1 = se0 + a.ld;
   long long i0, i1;
-  chunk_range(a, &i0, &i1);
+  chunk_range(a, ch, &i0, &i1);
   double p2 = 0.0;
   for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) {
     const T di = d[i];
@@ -211,12 +214,12 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_update_kernel(const CgArgs<T> a
     if (w1 != T(0)) se1[i] = fma(w1, di, se1[i]);
   }
   p2 = block_sum<kCgChunkNT>(p2, red);
-  if (threadIdx.x == 0) a.part2[(long long)c * a.nchunk + blockIdx.x] = p2;
+  if (threadIdx.x == 0) a.part2[(long long)c * a.nchunk + ch] = p2;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a) {
-  const int c = a.live[blockIdx.y];
+__device__ inline void cg_finish_body(const CgArgs<T>& a, int ch, int li) {
+  const int c = a.live[li];
   const ColState& st = a.st[c];
   const int phase = st.phase, l = st.l, m = st.m, n_est = st.n_est;
   const int J0 = st.J[0], J1 = st.J[1];
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a
   T* d = a.D + c * a.ld;
   T* se0 = a.SE + (long long)st.est_off * a.ld;
   long long i0, i1;
-  chunk_range(a, &i0, &i1);
+  chunk_range(a, ch, &i0, &i1);
   double dKd = 0.0, ee1 = 0.0;
   for (int k = 0; k < a.nchunk; ++k) {
     dKd += a.part1[(long long)c * a.nchunk + k];
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a
     if (phase == kPre)
       for (int t = 0; t < n_est; ++t)
         for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) se0[t * a.ld + i] = s[i];
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (ch == 0 && threadIdx.x == 0) {
       nx.outcome = 3;
       nx.phase = kDone;
       a.st_next[c] = nx;
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a
     const T btT = (T)(ee1 / st.ee);
     for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) d[i] = fma(btT, d[i], e[i]);
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (ch == 0 && threadIdx.x == 0) {
     nx.ee = ee1;
     nx.m = m1;
     nx.l = l1;
@@ -281,6 +284,40 @@ __global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a
     a.st_next[c] = nx;
     if (outcome == 4) atomicOr(a.status, kStatusMaxIter);
   }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_dot_kernel(const CgArgs<T> a) {
+  cg_dot_body(a, blockIdx.x, blockIdx.y);
+}
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_update_kernel(const CgArgs<T> a) {
+  cg_update_body(a, blockIdx.x, blockIdx.y);
+}
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_finish_kernel(const CgArgs<T> a) {
+  cg_finish_body(a, blockIdx.x, blockIdx.y);
+}
+
+// Batched forms: grid (chunk, live-list index, problem) over all problems of a batch; a
+// CTA past its problem's chunk count or live count returns at once.
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_dot_batch_kernel(const CgArgs<T>* __restrict__ args) {
+  const CgArgs<T>& a = args[blockIdx.z];
+  if ((int)blockIdx.y >= *a.n_live || (int)blockIdx.x >= a.nchunk) return;
+  cg_dot_body(a, blockIdx.x, blockIdx.y);
+}
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_update_batch_kernel(const CgArgs<T>* __restrict__ args) {
+  const CgArgs<T>& a = args[blockIdx.z];
+  if ((int)blockIdx.y >= *a.n_live || (int)blockIdx.x >= a.nchunk) return;
+  cg_update_body(a, blockIdx.x, blockIdx.y);
+}
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_finish_batch_kernel(const CgArgs<T>* __restrict__ args) {
+  const CgArgs<T>& a = args[blockIdx.z];
+  if ((int)blockIdx.y >= *a.n_live || (int)blockIdx.x >= a.nchunk) return;
+  cg_finish_body(a, blockIdx.x, blockIdx.y);
 }
 
 // Commit the state of the columns that just iterated (the first n_prev entries of the
@@ -294,6 +331,77 @@ __global__ void compact_kernel(ColState* __restrict__ st, const ColState* __rest
   for (int c = 0; c < R; ++c)
     if (st[c].phase != kDone) live[k++] = c;
   *n_live = k;
+}
+
+// Column bookkeeping of one problem of a batch (compact_batch_kernel).
+struct BatchCgProb {
+  ColState* st;
+  const ColState* st_next;
+  int* live;
+  int* n_live;
+  int R;
+  long long n;
+};
+
+// K V width bucket of the batched product for a largest live count r: 0..4 for r <= 2, 4,
+// 9, 17, 32 (the compiled widths of the batched kernel).
+__host__ __device__ inline int batch_width_bucket(int r) {
+  return r <= 2 ? 0 : r <= 4 ? 1 : r <= 9 ? 2 : r <= 17 ? 3 : 4;
+}
+
+// compact_kernel for every problem of a batch in one launch (one thread per problem; the
+// live lists and counts are those of the previous round, the counts 0 before the first):
+// commit, rebuild, and the largest live count to *rmax.  Inside a step graph it also sets
+// the loop condition (another round while any column is live) and the branch (the width
+// bucket of rmax; none when 0).  A round cap stops a loop that would not end.
+// stat (may be null): [rounds, sum of n_b^2 x live columns, launches, rounds this call].
+__global__ void __launch_bounds__(256) compact_batch_kernel(
+    const BatchCgProb* __restrict__ probs, int B, int* __restrict__ rmax, int in_graph,
+    cudaGraphConditionalHandle h_loop, cudaGraphConditionalHandle h_branch, int max_rounds,
+    long long* __restrict__ stat, int* __restrict__ status) {
+  __shared__ int s_max[256];
+  __shared__ long long s_ent[256];
+  int mx = 0;
+  long long ent = 0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const BatchCgProb P = probs[b];
+    const int n_prev = *P.n_live;
+    for (int k = 0; k < n_prev; ++k) P.st[P.live[k]] = P.st_next[P.live[k]];
+    int k = 0;
+    for (int c = 0; c < P.R; ++c)
+      if (P.st[c].phase != kDone) P.live[k++] = c;
+    *P.n_live = k;
+    mx = max(mx, k);
+    ent += P.n * P.n * (long long)k;
+  }
+  s_max[threadIdx.x] = mx;
+  s_ent[threadIdx.x] = ent;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int t = 1; t < (int)blockDim.x; ++t) {
+    mx = max(mx, s_max[t]);
+    ent += s_ent[t];
+  }
+  if (stat) {
+    const long long it = stat[3]++;
+    if (mx > 0 && it >= max_rounds) {
+      atomicOr(status, kStatusMaxIter);
+      for (int b = 0; b < B; ++b) *probs[b].n_live = 0;
+      mx = 0;
+      ent = 0;
+    }
+    stat[2] += 1;
+    if (mx > 0) {
+      stat[0] += 1;
+      stat[1] += ent;
+      stat[2] += 4;   // the batched K V and the three batched CG launches
+    }
+  }
+  *rmax = mx;
+  if (in_graph) {
+    cudaGraphSetConditional(h_loop, mx > 0 ? 1u : 0u);
+    cudaGraphSetConditional(h_branch, mx > 0 ? (unsigned)batch_width_bucket(mx) : 5u);
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -356,12 +464,20 @@ __global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__
 __global__ void sgld_chain_kernel(double* __restrict__ psi, const double* __restrict__ g,
                                   const double* __restrict__ M, const double* __restrict__ prior,
                                   int p, unsigned long long seed, ChainSlot* __restrict__ cs,
-                                  int* __restrict__ status) {
+                                  int* __restrict__ status, int advance = 1,
+                                  int trace_stride = 0, int trace_off = 0) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const long long k = cs->k;
+  const long long stride = trace_stride > 0 ? trace_stride : p;
   sgld_body(psi, g, M, prior, cs->eps[k], p, seed, cs->step0 + (unsigned long long)k,
-            cs->trace ? cs->trace + k * p : nullptr, status);
-  cs->k = k + 1;
+            cs->trace ? cs->trace + k * stride + trace_off : nullptr, status);
+  if (advance) cs->k = k + 1;
+}
+
+// The chain slot moves on to the next step (batched step graphs: after every problem's
+// update).
+__global__ void chain_advance_kernel(ChainSlot* __restrict__ cs) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) cs->k += 1;
 }
 
 // Graph form of compact_kernel: commits the previous iteration's column states (the live

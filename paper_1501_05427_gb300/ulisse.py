@@ -34,7 +34,7 @@ EXPORTED = [
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
-    "ulisse_set_graph", "ulisse_autotune",
+    "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain",
 ]
 
 
@@ -132,6 +132,7 @@ def load():
     lib.ulisse_batch_kmv.argtypes = [P, P, P, I, P]
     lib.ulisse_batch_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_batch_sgld_step.argtypes = [P, P, D, U64, P]
+    lib.ulisse_batch_sgld_chain.argtypes = [P, P, P, I, U64, P]
     lib.ulisse_set_graph.argtypes = [P, I]
     lib.ulisse_autotune.argtypes = [P, P, I, I, ctypes.POINTER(ulisse_tune_entry)]
     lib.ulisse_last_error.argtypes = [P]
@@ -488,6 +489,16 @@ class BatchContext:
         return psi, g
 
     counters = Context.counters
+    set_graph = Context.set_graph
+
+    def sgld_chain(self, psi_dev, eps_dev, step0=0, trace_dev=None, allow=()):
+        """len(eps_dev) batched SGLD steps with the packed psi resident on the device."""
+        st = self._lib.ulisse_batch_sgld_chain(
+            self._h, ctypes.c_void_p(psi_dev.data_ptr()), ctypes.c_void_p(eps_dev.data_ptr()),
+            int(eps_dev.numel()), step0,
+            ctypes.c_void_p(trace_dev.data_ptr()) if trace_dev is not None else None)
+        self._check(st, allow)
+        return psi_dev
 
 
 def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
@@ -569,3 +580,7 @@ def ulisse_set_graph(ctx: Context, enable=True):
 
 def ulisse_autotune(ctx: Context, psi, max_cols=None, reps=3):
     return ctx.autotune(psi, max_cols, reps)
+
+
+def ulisse_batch_sgld_chain(ctx: BatchContext, psi_dev, eps_dev, step0=0, trace_dev=None):
+    return ctx.sgld_chain(psi_dev, eps_dev, step0, trace_dev)

@@ -2,6 +2,7 @@
 all of them in one persistent launch.  Each problem is checked against the FP64 oracle with
 the generator seed the batch gives it (cfg.seed + b), and against a single context."""
 import math
+import time
 
 import numpy as np
 import pytest
@@ -184,3 +185,54 @@ def test_batch_argument_errors():
             bc.grad(bad)
         n, p = u.ulisse_batch_size(bc)
         assert (n, p) == (2, bc.n_params)
+
+
+def test_batch_graph_chain_matches_host_loop():
+    """Every batched step as one graph launch (WHILE / SWITCH nodes around the persistent
+    launches) reproduces the host loop bit for bit: trace, final parameters, counters."""
+    spec = [(2200, 2), (700, 4), (3100, 8), (150, 8), (1800, 4)]
+    probs = [w.random_problem(n, d, seed=4000 + n) for n, d in spec]
+    psi0 = np.concatenate([p.psi_true for p in probs])
+    out = []
+    with _batch(probs, n_probes=8, seed=12) as bc:
+        for graph in (False, True, True):
+            bc.set_graph(graph)
+            psi = torch.tensor(psi0, dtype=torch.float64, device="cuda")
+            eps = torch.full((4,), 1e-3, dtype=torch.float64, device="cuda")
+            tr = torch.zeros((4, bc.n_params), dtype=torch.float64, device="cuda")
+            c0 = bc.counters()
+            bc.sgld_chain(psi, eps, step0=20, trace_dev=tr)
+            c1 = bc.counters()
+            out.append((tr.cpu().numpy(), psi.cpu().numpy(),
+                        tuple(b - a for a, b in zip(c0, c1))))
+        # one step through the host-buffer call equals the chain's first step
+        bc.set_graph(True)
+        psi_h, g_h = bc.sgld_step(psi0, 1e-3, step=20)
+    (tr_h, psi_hl, w_h), (tr_g, psi_g, w_g), (tr_g2, _, w_g2) = out
+    assert np.array_equal(tr_g, tr_h) and np.array_equal(psi_g, psi_hl)
+    assert np.array_equal(tr_g2, tr_h)
+    assert w_g == w_h == w_g2
+    assert np.array_equal(psi_h, tr_h[0])
+
+
+def test_batch_graph_uneven_workload():
+    """The 64-problem workload, two batched steps as graph launches: finite parameters,
+    the same trace as the host loop."""
+    probs = w.uneven_batch()
+    psi0 = np.concatenate([p.psi_true for p in probs])
+    traces = []
+    with _batch(probs, n_probes=8, seed=5) as bc:
+        for graph in (True, False):
+            bc.set_graph(graph)
+            psi = torch.tensor(psi0, dtype=torch.float64, device="cuda")
+            eps = torch.full((2,), 1e-4, dtype=torch.float64, device="cuda")
+            tr = torch.zeros((2, bc.n_params), dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            bc.sgld_chain(psi, eps, step0=0, trace_dev=tr)
+            torch.cuda.synchronize()
+            print("uneven batch (64 problems), %s: %.1f ms per batched step"
+                  % ("graph" if graph else "host loop", 1e3 * (time.perf_counter() - t0) / 2))
+            traces.append(tr.cpu().numpy())
+    assert np.all(np.isfinite(traces[0]))
+    assert np.array_equal(traces[0], traces[1])
