@@ -64,7 +64,7 @@ KMV_KERNELS = {
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -76,6 +76,9 @@ def parse_args():
                     help="skip timing the plain FP32 path beside the chosen one")
     ap.add_argument("--no-graph", action="store_true",
                     help="run the steps from the host loop instead of one graph launch each")
+    ap.add_argument("--workload", choices=["census_like", "uneven_batch"], default="census_like",
+                    help="census_like: the headline; uneven_batch: 64 problems of uneven size "
+                         "advanced together (batched context, one graph launch per step)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the K V autotuner (untuned launch configurations)")
     ap.add_argument("--profile-steps", type=int, default=8,
@@ -510,10 +513,92 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """The 64-problem uneven workload: one batched SGLD step of all problems per graph launch
+    (persistent K V and gradient launches over all problems)."""
+    import numpy as np
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+
+    world, rank, local = dist_setup(args, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    probs = w.uneven_batch()
+    stream = torch.cuda.current_stream(dev)
+    # the slowest of 576 columns decides a batched step's rounds; a column that has not
+    # stopped after max_iter CG iterations is cut off (reported, not fatal)
+    cfg = u.ulisse_config_default(n_probes=8, probe_kind=u.PROBE_RADEMACHER, q=1.0, beta=1.0,
+                                  eps=1e-8, max_iter=3000, seed=20150126 + 1000 * rank)
+    allow = (u.ULISSE_ERR_MAXITER,)
+    cut = [0]
+    Xs = [torch.from_numpy(p.X).to(dev) for p in probs]
+    ys = [torch.from_numpy(p.y).to(dev) for p in probs]
+    bc = u.BatchContext(Xs, ys, cfg, stream=stream)
+    bc.set_graph(not args.no_graph)
+    K, W = args.steps, args.warmup
+    psi = torch.tensor(np.concatenate([p.psi_true for p in probs]), dtype=torch.float64,
+                       device=dev)
+    eps = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    for k in range(W):
+        bc.sgld_chain(psi, eps[:1], step0=k, allow=allow)
+    c0 = bc.counters()
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(K)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    torch.cuda.synchronize(dev)
+    rounds = []
+    for k in range(K):
+        flush.zero_()
+        events[k][0].record(stream)
+        st = bc.sgld_chain_status(psi, eps[k:k + 1], step0=W + k)
+        events[k][1].record(stream)
+        cut[0] += int(st == u.ULISSE_ERR_MAXITER)
+        rounds.append(bc.counters()[0])
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    c1 = bc.counters()
+    rounds = [b - a for a, b in zip([c0[0]] + rounds[:-1], rounds)]
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_ms = sum(step_ms)
+    n_sum = sum(p.n for p in probs)
+    line = {
+        "metric": "SGLD steps/s", "value": world * K * len(probs) / (total_ms / 1000.0),
+        "unit": "problem-steps/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "uneven_batch", "problems": len(probs), "n_total": n_sum,
+                   "n_min": min(p.n for p in probs), "n_max": max(p.n for p in probs),
+                   "dims": sorted(set(p.d for p in probs)), "n_probes": 8,
+                   "step_form": "host loop" if args.no_graph else "one CUDA graph launch per batched step",
+                   "l2": "flushed between timed steps (512 MiB write)"},
+        "batched_steps_per_s": K / (total_ms / 1000.0),
+        "kv_throughput": {"value": (c1[1] - c0[1]) / (total_ms / 1000.0),
+                          "unit": "entry·RHS/s (whole step: K V rounds and the gradient sweep)"},
+        "mvp_rounds_per_step": (c1[0] - c0[0]) / K,
+        "rounds_per_step": rounds,
+        "steps_with_a_column_cut_at_max_iter": cut[0],
+        "gpu_launches": int(c1[2] - c0[2]),
+        "clocks": clocks,
+        "step_ms": step_ms,
+    }
+    bc.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven_batch":
+        return run_batch(args)
     return run_ours(args)
 
 

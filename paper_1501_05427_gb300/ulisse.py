@@ -491,14 +491,19 @@ class BatchContext:
     counters = Context.counters
     set_graph = Context.set_graph
 
-    def sgld_chain(self, psi_dev, eps_dev, step0=0, trace_dev=None, allow=()):
+    def sgld_chain_status(self, psi_dev, eps_dev, step0=0, trace_dev=None):
+        """As sgld_chain; returns the status instead of raising on ULISSE_ERR_MAXITER."""
+        return self.sgld_chain(psi_dev, eps_dev, step0, trace_dev, allow=(ULISSE_ERR_MAXITER,),
+                               status=True)
+
+    def sgld_chain(self, psi_dev, eps_dev, step0=0, trace_dev=None, allow=(), status=False):
         """len(eps_dev) batched SGLD steps with the packed psi resident on the device."""
         st = self._lib.ulisse_batch_sgld_chain(
             self._h, ctypes.c_void_p(psi_dev.data_ptr()), ctypes.c_void_p(eps_dev.data_ptr()),
             int(eps_dev.numel()), step0,
             ctypes.c_void_p(trace_dev.data_ptr()) if trace_dev is not None else None)
         self._check(st, allow)
-        return psi_dev
+        return st if status else psi_dev
 
 
 def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
