@@ -64,7 +64,7 @@ KMV_KERNELS = {
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=600)
+    ap.add_argument("--steps", type=int, default=150)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
@@ -276,11 +276,16 @@ def run_reference(args):
 
 def _timed_steps(ctx, dev, stream, psi0, K, W, step_base, flush, barrier, sampler=None):
     """W untimed steps, then K steps each bracketed by CUDA events on the library's stream,
-    with an L2 flush (outside the spans) before each."""
+    with an L2 flush (outside the spans) before each.  Every step starts from psi0 with its
+    own step number (its own probes and truncation draws): with a constant step size the
+    heavy-tailed gradient estimate lets a long chain jump far from the posterior, and the
+    throughput is measured at the workload's parameters."""
     import torch
-    psi_dev = torch.tensor(psi0, dtype=torch.float64, device=dev)
+    psi_start = torch.tensor(psi0, dtype=torch.float64, device=dev)
+    psi_dev = psi_start.clone()
     eps_dev = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
     for k in range(W):
+        psi_dev.copy_(psi_start)
         ctx.sgld_chain(psi_dev, eps_dev[:1], step0=step_base + k)
     c0 = ctx.counters()
     events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -291,6 +296,7 @@ def _timed_steps(ctx, dev, stream, psi0, K, W, step_base, flush, barrier, sample
     torch.cuda.synchronize(dev)
     rounds = []
     for k in range(K):
+        psi_dev.copy_(psi_start)          # every step from the same parameters (see DESIGN)
         flush.zero_()
         events[k][0].record(stream)
         ctx.sgld_chain(psi_dev, eps_dev[k:k + 1], step0=step_base + W + k)
@@ -398,16 +404,15 @@ def run_ours(args):
     prof = _profile_pass(ctx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
 
     # end to end through the host-buffer API (psi in, psi and g out every step), replaying
-    # exactly the timed steps: same start, same step numbers, hence the same draws and rounds
-    psi_h = prob.psi_true.copy()
+    # exactly the timed steps: same parameters, same step numbers, so the same draws and rounds
     for k in range(W):
-        psi_h, _ = ctx.sgld_step(psi_h, EPS_T, step=k)
+        ctx.sgld_step(prob.psi_true.copy(), EPS_T, step=k)
     barrier()
     torch.cuda.synchronize(dev)
     r_e0 = ctx.counters()[0]
     t0 = time.perf_counter()
     for k in range(K):
-        psi_h, g_h = ctx.sgld_step(psi_h, EPS_T, step=W + k)
+        psi_h, g_h = ctx.sgld_step(prob.psi_true.copy(), EPS_T, step=W + k)
     torch.cuda.synchronize(dev)
     e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_rounds = (ctx.counters()[0] - r_e0) / max(K, 1)
@@ -542,7 +547,9 @@ def run_batch(args):
                        device=dev)
     eps = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    psi_start = psi.clone()
     for k in range(W):
+        psi.copy_(psi_start)
         bc.sgld_chain(psi, eps[:1], step0=k, allow=allow)
     c0 = bc.counters()
     events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -552,6 +559,7 @@ def run_batch(args):
     torch.cuda.synchronize(dev)
     rounds = []
     for k in range(K):
+        psi.copy_(psi_start)
         flush.zero_()
         events[k][0].record(stream)
         st = bc.sgld_chain_status(psi, eps[k:k + 1], step0=W + k)
