@@ -69,8 +69,13 @@ typedef struct {
     int probe_kind;          /* ulisse_probe_kind */
     int probe_refresh;       /* redraw the probes every probe_refresh steps (>= 1; the paper's
                                 Concrete run used 20, Sec. 5.1); epoch = step / probe_refresh */
-    int warm_start_probes;   /* nonzero: while the probes are unchanged, start each probe
-                                solve from the previous step's final CG iterate (Sec. 5.1) */
+    int warm_start_probes;   /* nonzero: start each solve from the previous step's final CG
+                                iterate of its column while the right-hand side is unchanged
+                                -- y always, the probes within a refresh epoch (Sec. 5.1's
+                                reuse of probes and solutions); one extra K V round forms the
+                                initial residuals, and an iterate is kept only when it lowers
+                                the residual (no random draw: the estimates stay unbiased).
+                                Single contexts only. */
     double q;                /* early-stop threshold alpha = q sqrt(n) (Sec. 4; the paper uses q=1) */
     double beta;             /* ULISSE weights w_r = exp(beta r) (Sec. 4; the paper uses beta=1) */
     double eps;              /* CG convergence threshold on ||e|| (Algorithm 1; paper: 1e-8) */

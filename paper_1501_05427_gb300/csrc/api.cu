@@ -80,6 +80,9 @@ struct ulisse_ctx {
   std::vector<void*> ws_allocs;
 
   int meta_grad_R = -1;       // column count the gradient's column metadata was uploaded for
+  int* warm_valid = nullptr;  // device: Sbest holds the iterates of a finished step's solve
+  void* Sbest = nullptr;      // cap columns right after S (one allocation), see CgArgs
+  int* warm_map = nullptr;    // K s_0 column maps of warm-started solves (2 x cap): S/Sbest
 
   // autotuned K V launch configuration per live column count (ulisse_autotune); index
   // nl - 1, empty until tuned
@@ -233,9 +236,12 @@ static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
   dev_free(reinterpret_cast<void*&>(ctx->part2));
   dev_free(reinterpret_cast<void*&>(ctx->live));
   dev_free(reinterpret_cast<void*&>(ctx->iota));
+  dev_free(reinterpret_cast<void*&>(ctx->warm_map));
   const size_t col = (size_t)ctx->ldn * ctx->esz;
-  for (void** p : {&ctx->B, &ctx->S, &ctx->E, &ctx->D, &ctx->KD})
+  for (void** p : {&ctx->B, &ctx->E, &ctx->D, &ctx->KD})
     CKS(dev_alloc(ctx, p, col * cap));
+  CKS(dev_alloc(ctx, &ctx->S, col * cap * 2));   // S, then Sbest
+  ctx->Sbest = (char*)ctx->S + col * cap;
   CKS(dev_alloc(ctx, &ctx->SE, col * cap_est));
   CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->st), sizeof(ColState) * cap));
   CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->st_next), sizeof(ColState) * cap));
@@ -247,6 +253,14 @@ static ulisse_status ensure_columns(ulisse_ctx* ctx, int R, int R_est) {
   std::vector<int> io(ni);
   for (int i = 0; i < ni; ++i) io[i] = i;
   CK(cudaMemcpyAsync(ctx->iota, io.data(), sizeof(int) * ni, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  // warm-started solves read s_0 from Sbest (column cap + c); with the learned warm start
+  // column 0 comes from S
+  CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->warm_map), sizeof(int) * 2 * cap));
+  std::vector<int> wm(2 * cap);
+  for (int c = 0; c < cap; ++c) wm[c] = wm[cap + c] = cap + c;
+  wm[cap] = 0;
+  CK(cudaMemcpyAsync(ctx->warm_map, wm.data(), sizeof(int) * 2 * cap, cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   ctx->cap = cap;
@@ -481,6 +495,11 @@ static CgArgs<T> cg_args(ulisse_ctx* ctx, int has_s0, unsigned long long step) {
   a.seed = ctx->cfg.seed;
   a.step = step;
   a.cs = nullptr;
+  a.n_live = nullptr;
+  a.warm_refresh = 0;
+  a.warm_valid = ctx->warm_valid;
+  a.y_learned = 0;
+  a.Sbest = (T*)ctx->Sbest;
   a.status = ctx->status_dev;
   return a;
 }
@@ -506,10 +525,19 @@ static ulisse_status upload_meta(ulisse_ctx* ctx, int R, const int* n_est, int* 
 // Batched CG + ULISSE on columns 0..R-1 of B (S holds s_0 when has_s0).  The host learns
 // the live count after every iteration and launches K V on the live columns only.
 // s0_cols > 0: columns 0..s0_cols-1 of S hold initial iterates (the rest are zero).
+// warm: every column's previous final iterate is in S (cg_init decides per column which to
+// keep, see CgArgs); y_learned: column 0 holds the learned warm start instead.
 template <typename T>
-static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned long long step) {
+static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned long long step,
+                                bool warm = false, bool y_learned = false) {
   CgArgs<T> a = cg_args<T>(ctx, s0_cols > 0, step);
-  if (s0_cols > 0) {
+  if (warm) {
+    a.warm_refresh = ctx->cfg.probe_refresh;
+    a.y_learned = y_learned ? 1 : 0;
+    CKS(run_kmv(ctx, ctx->S, ctx->warm_map + (y_learned ? ctx->cap : 0), R, ctx->KD, ctx->iota,
+                kModeK, -1));
+    ctx->mvp_rounds += 1;
+  } else if (s0_cols > 0) {
     if (s0_cols < R)
       CK(cudaMemsetAsync((char*)ctx->KD + (size_t)s0_cols * ctx->ldn * ctx->esz, 0,
                          (size_t)(R - s0_cols) * ctx->ldn * ctx->esz, ctx->stream));
@@ -552,9 +580,10 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned lo
 }
 
 static ulisse_status solve_dispatch(ulisse_ctx* ctx, int R, int s0_cols,
-                                    unsigned long long step) {
-  return ctx->f64 ? solve_core<double>(ctx, R, s0_cols, step)
-                  : solve_core<float>(ctx, R, s0_cols, step);
+                                    unsigned long long step, bool warm = false,
+                                    bool y_learned = false) {
+  return ctx->f64 ? solve_core<double>(ctx, R, s0_cols, step, warm, y_learned)
+                  : solve_core<float>(ctx, R, s0_cols, step, warm, y_learned);
 }
 
 // Gradient column maps: left factors SE[0] (a1) and SE[2..1+nr] (z_j) with scales 1/2 and
@@ -672,17 +701,22 @@ static ulisse_status grad_core(ulisse_ctx* ctx, unsigned long long step,
   }
   if (prologue_only) return ULISSE_OK;
   int s0_cols = 0;
-  if (ctx->ws_use && ctx->ws_trained) {
-    // learned warm start for the y column; the probe columns start from zero
+  const bool warm = ctx->cfg.warm_start_probes != 0;
+  const bool learned = ctx->ws_use && ctx->ws_trained;
+  if (learned) {
+    // learned warm start for the y column; the probe columns start from zero (or, with
+    // warm-started solves, from their previous iterates)
     ws_x0(ctx->wsb, ctx->psi_dev, true, (const float*)ctx->xhat, ctx->DP, ctx->n, ctx->params,
           ctx->ws_c, (float*)ctx->S, ctx->num_sms, ctx->stream);
     CK(cudaGetLastError());
     ctx->launches += 2;
-    CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0, (size_t)(R - 1) * ctx->ldn * ctx->esz,
-                       ctx->stream));
+    if (!warm)
+      CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0,
+                         (size_t)(R - 1) * ctx->ldn * ctx->esz, ctx->stream));
     s0_cols = 1;
   }
-  CKS(solve_dispatch(ctx, R, s0_cols, step));
+  CKS(solve_dispatch(ctx, R, warm ? 0 : s0_cols, step, warm, learned));
+  if (warm) CK(cudaMemsetAsync(ctx->warm_valid, 0x01, sizeof(int), ctx->stream));
   if (ctx->ws_record) {
     ws_record(ctx->wsb, ctx->psi_dev, (const float*)ctx->y, (const float*)ctx->xhat, ctx->DP,
               ctx->params, ctx->ws_next % ctx->wsb.max_pairs, (unsigned long long)ctx->ws_next,
@@ -722,8 +756,6 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
   if (n < 1 || n > 2147483647LL) return fail(nullptr, ULISSE_ERR_ARG, "n out of range");
   if (d < 1 || d > kMaxD) return fail(nullptr, ULISSE_ERR_ARG, "d must be in 1..16");
   if (check_cfg(cfg) != ULISSE_OK) return fail(nullptr, ULISSE_ERR_ARG, "invalid config");
-  if (cfg->warm_start_probes)
-    return fail(nullptr, ULISSE_ERR_ARG, "warm_start_probes is not available in this build");
   ulisse_ctx* ctx = new ulisse_ctx();
   ctx->stream = (cudaStream_t)stream;
   ctx->cfg = *cfg;
@@ -760,7 +792,8 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bmap), sizeof(int) * kMaxM)) ||
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->M_dev), sizeof(double) * kMaxP * kMaxP)) ||
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->prior_dev), sizeof(double) * kMaxP)) ||
-      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))))
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))) ||
+      (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->warm_valid), sizeof(int))))
     return bail(s);
   if (ctx->mixed) {
     if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bneg), sizeof(float) * ctx->ld128)) ||
@@ -921,6 +954,7 @@ ulisse_status ulisse_solve(ulisse_ctx* ctx, const double* psi, const float* B, i
   CKS(prescale(ctx));
   CKS(ensure_columns(ctx, R, tot));
   CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->warm_valid, 0, sizeof(int), ctx->stream));   // S is overwritten
   const long long n = ctx->n;
   auto in_cols = [&](const float* src, void* dst) -> ulisse_status {
     if (!ctx->f64) {
@@ -1081,18 +1115,28 @@ static ulisse_status graph_capture_body(ulisse_ctx* ctx, int s0_cols) {
                                                 ctx->cfg.probe_kind, ctx->cfg.seed, 0,
                                                 ctx->chain, ctx->cfg.probe_refresh);
   CK(cudaGetLastError());
+  const bool warm = ctx->cfg.warm_start_probes != 0;
   if (s0_cols > 0) {
     ws_x0(ctx->wsb, ctx->psi_dev, true, (const float*)ctx->xhat, ctx->DP, ctx->n, ctx->params,
           ctx->ws_c, (float*)ctx->S, ctx->num_sms, ctx->stream);
     CK(cudaGetLastError());
-    CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0,
-                       (size_t)(R - 1) * ctx->ldn * ctx->esz, ctx->stream));
-    CK(cudaMemsetAsync((char*)ctx->KD + (size_t)s0_cols * ctx->ldn * ctx->esz, 0,
-                       (size_t)(R - s0_cols) * ctx->ldn * ctx->esz, ctx->stream));
-    CKS(run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1));
+    if (!warm) {
+      CK(cudaMemsetAsync((char*)ctx->S + ctx->ldn * ctx->esz, 0,
+                         (size_t)(R - 1) * ctx->ldn * ctx->esz, ctx->stream));
+      CK(cudaMemsetAsync((char*)ctx->KD + (size_t)s0_cols * ctx->ldn * ctx->esz, 0,
+                         (size_t)(R - s0_cols) * ctx->ldn * ctx->esz, ctx->stream));
+      CKS(run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1));
+    }
   }
-  CgArgs<T> a = cg_args<T>(ctx, s0_cols > 0, 0);
+  if (warm)
+    CKS(run_kmv(ctx, ctx->S, ctx->warm_map + (s0_cols > 0 ? ctx->cap : 0), R, ctx->KD,
+                ctx->iota, kModeK, -1));
+  CgArgs<T> a = cg_args<T>(ctx, s0_cols > 0 && !warm, 0);
   a.cs = ctx->chain;
+  if (warm) {
+    a.warm_refresh = ctx->cfg.probe_refresh;
+    a.y_learned = s0_cols > 0 ? 1 : 0;
+  }
   cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
   CK(cudaGetLastError());
   CK(cudaMemsetAsync(ctx->n_live_dev, 0, sizeof(int), ctx->stream));
@@ -1162,6 +1206,7 @@ static ulisse_status graph_capture_body(ulisse_ctx* ctx, int s0_cols) {
     CK(e4);
   }
   // after the loop: the second estimate of K^{-1} y as the right factor, gradient, update
+  if (warm) CK(cudaMemsetAsync(ctx->warm_valid, 0x01, sizeof(int), ctx->stream));
   CK(cudaMemcpyAsync(ctx->B, (char*)ctx->SE + ctx->ldn * ctx->esz, ctx->ldn * ctx->esz,
                      cudaMemcpyDeviceToDevice, ctx->stream));
   CKS(run_grad(ctx, R));
@@ -1199,6 +1244,10 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
     r = run_kmv(ctx, ctx->D, ctx->live, k, ctx->KD, ctx->live, kModeK, -1);
   if (r == ULISSE_OK && s0_cols > 0)
     r = run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1);
+  const bool warm = ctx->cfg.warm_start_probes != 0;
+  if (r == ULISSE_OK && warm)
+    r = run_kmv(ctx, ctx->S, ctx->warm_map + (s0_cols > 0 ? ctx->cap : 0), R, ctx->KD, ctx->iota,
+                kModeK, -1);
   if (r == ULISSE_OK) r = run_grad(ctx, R);
   ctx->planning = false;
   if (r != ULISSE_OK) {
@@ -1229,10 +1278,11 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
   CK(cudaGraphInstantiate(&ctx->step_exec, graph, 0));
   // what one launch does outside the CG loop (the loop's share is counted on the device)
   const long long kmv_per = ctx->mixed ? 2 : 1, kmv_cols = ctx->mixed ? 64 : kMaxRChunk;
-  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + 1 + 1 +
-      (s0_cols > 0 ? 2 + kmv_per * ((s0_cols + kmv_cols - 1) / kmv_cols) : 0);
-  ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + s0_cols);
-  ctx->graph_rounds_fixed = s0_cols > 0 ? 1 : 0;
+  const int init_cols = warm ? R : s0_cols;   // columns of the product K s_0
+  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + 1 + 1 + (s0_cols > 0 ? 2 : 0) +
+      (init_cols > 0 ? kmv_per * ((init_cols + kmv_cols - 1) / kmv_cols) : 0);
+  ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + init_cols);
+  ctx->graph_rounds_fixed = init_cols > 0 ? 1 : 0;
   ctx->graph_key = s0_cols;
   return ULISSE_OK;
 }
@@ -1634,6 +1684,8 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
   if (cfg->precision != ULISSE_PREC_FP32)
     return fail(nullptr, ULISSE_ERR_ARG, "batched contexts run the FP32 path");
   if (cfg->n_probes > 16) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take n_probes <= 16");
+  if (cfg->warm_start_probes)
+    return fail(nullptr, ULISSE_ERR_ARG, "batched contexts do not warm-start their solves");
   for (int b = 0; b < n_problems; ++b)
     if (d[b] < 1 || d[b] > kBatchMaxDP) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take d <= 8");
   ulisse_ctx* ctx = new ulisse_ctx();
@@ -2354,7 +2406,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->g_dev), &ctx->sa_dev,
                    reinterpret_cast<void**>(&ctx->amap), reinterpret_cast<void**>(&ctx->bmap),
                    reinterpret_cast<void**>(&ctx->M_dev), reinterpret_cast<void**>(&ctx->prior_dev),
-                   reinterpret_cast<void**>(&ctx->status_dev)})
+                   reinterpret_cast<void**>(&ctx->status_dev),
+                   reinterpret_cast<void**>(&ctx->warm_valid)})
     dev_free(*p);
   for (void* p : ctx->ws_allocs) cudaFree(p);
   ctx->ws_allocs.clear();

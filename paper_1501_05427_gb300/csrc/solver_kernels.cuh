@@ -64,6 +64,16 @@ struct CgArgs {
   unsigned long long seed, step;
   const ChainSlot* cs;   // when set, the step number comes from the chain slot
   const int* n_live;     // batched launches: this problem's live column count
+  // Warm-started solves (Sec. 5.1's probe reuse): when warm_refresh > 0, S holds the final
+  // CG iterates of the previous step's solve of every column (valid while *warm_valid is
+  // nonzero).  Column 0 (y, never changes) starts from its iterate -- or from the learned
+  // warm start when y_learned -- and probe columns start from theirs while the probes are
+  // unchanged (step % warm_refresh != 0).  The keep-if-better rule still applies.
+  int warm_refresh;
+  const int* warm_valid;
+  int y_learned;
+  T* Sbest;              // warm-started solves: per column, the iterate of smallest residual
+                         // seen (the start of the next step's solve)
   int* status;
 };
 
@@ -99,6 +109,17 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   T* d = a.D + c * a.ld;
   const T* b = a.B + c * a.ld;
   const T* ks0 = a.KD + c * a.ld;
+  const bool warm = a.warm_refresh > 0;
+  T* sb = warm ? a.Sbest + c * a.ld : nullptr;
+  // with warm-started solves the start comes from Sbest (y_learned: column 0 from S)
+  const T* s0 = (warm && !(c == 0 && a.y_learned)) ? sb : s;
+  bool use_s0 = a.has_s0 != 0;
+  if (warm) {
+    const unsigned long long step = a.cs ? a.cs->step0 + (unsigned long long)a.cs->k : a.step;
+    const bool valid = *a.warm_valid != 0;
+    use_s0 = (c == 0) ? (a.y_learned || valid)
+                      : (valid && step % (unsigned long long)a.warm_refresh != 0);
+  }
   // An initial iterate is kept only when it lowers the residual norm below that of s_0 = 0.
   // The choice depends on the parameters, the data and the iterate alone (no random draw),
   // so every estimator built on it stays unbiased.
@@ -106,16 +127,18 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
     const double bi = (double)b[i];
     pb += bi * bi;
-    if (a.has_s0) {
+    if (use_s0) {
       const double ri = (double)(T)(b[i] - ks0[i]);
       pr += ri * ri;
     }
   }
   const double bb = block_sum<kCgNT>(pb, red);
-  const double rr = a.has_s0 ? block_sum<kCgNT>(pr, red) : bb;
-  const bool keep = a.has_s0 && rr < bb;
+  const double rr = use_s0 ? block_sum<kCgNT>(pr, red) : bb;
+  const bool keep = use_s0 && rr < bb;
   for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
-    if (!keep) s[i] = T(0);
+    const T si = keep ? s0[i] : T(0);
+    s[i] = si;
+    if (warm) sb[i] = si;
     const T ei = keep ? b[i] - ks0[i] : b[i];
     e[i] = ei;
     d[i] = ei;
@@ -132,6 +155,7 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   __syncthreads();
   if (threadIdx.x == 0) {
     st.ee = ee;
+    st.best_ee = ee;
     st.l = 0;
     st.m = 0;
     st.outcome = 0;
@@ -271,12 +295,20 @@ __device__ inline void cg_finish_body(const CgArgs<T>& a, int ch, int li) {
   if (copy_s)
     for (int t = 0; t < n_est; ++t)
       for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) se0[t * a.ld + i] = s[i];
+  // warm-started solves: remember the iterate of smallest residual (same decision in every
+  // CTA of the column)
+  const bool better = a.warm_refresh > 0 && ee1 < st.best_ee;
+  if (better) {
+    T* sb = a.Sbest + c * a.ld;
+    for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) sb[i] = s[i];
+  }
   if (!done) {
     const T btT = (T)(ee1 / st.ee);
     for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) d[i] = fma(btT, d[i], e[i]);
   }
   if (ch == 0 && threadIdx.x == 0) {
     nx.ee = ee1;
+    if (better) nx.best_ee = ee1;
     nx.m = m1;
     nx.l = l1;
     nx.outcome = outcome;

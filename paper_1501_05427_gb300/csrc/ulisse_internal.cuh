@@ -51,6 +51,7 @@ struct ColState {
   int est_off;    // first estimator column in the estimate buffer
   int colid;      // random-stream column index
   int pad;
+  double best_ee; // warm-started solves: smallest e^T e seen (its iterate is kept in Sbest)
 };
 
 // ------------------------------------------------------------------------------------
