@@ -81,6 +81,10 @@ def parse_args():
                          "advanced together (batched context, one graph launch per step)")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the K V autotuner (untuned launch configurations)")
+    ap.add_argument("--refresh", type=int, default=20,
+                    help="chosen path: redraw the probes every this many steps (Sec. 5.1 uses 20)")
+    ap.add_argument("--no-warm", action="store_true",
+                    help="chosen path: start every solve from zero (no warm-started solves)")
     ap.add_argument("--profile-steps", type=int, default=8,
                     help="steps of the event-timed pass (per-launch K V times)")
     return ap.parse_args()
@@ -374,15 +378,16 @@ def run_ours(args):
 
     tuned = {}
 
-    def make_ctx(path):
+    def make_ctx(path, refresh, warm, key):
         prec = u.PREC_MIXED if path == "mixed" else u.PREC_FP32
         cfg = u.ulisse_config_default(n_probes=N_PROBES, probe_kind=u.PROBE_RADEMACHER, q=1.0,
                                       beta=1.0, eps=1e-8, max_iter=1000,
-                                      seed=20150123 + rank, precision=prec)
+                                      seed=20150123 + rank, precision=prec,
+                                      probe_refresh=refresh, warm_start_probes=int(warm))
         c = u.Context(X, y, cfg, stream=stream)
         c.set_graph(not args.no_graph)
         if not args.no_tune:
-            tuned[path] = c.autotune(prob.psi_true, R, reps=3)
+            tuned[key] = c.autotune(prob.psi_true, R, reps=3)
         return c
 
     def max_over_ranks(v):
@@ -393,7 +398,8 @@ def run_ours(args):
         return v
 
     # chosen path: the timed region
-    ctx = make_ctx(args.path)
+    warm = not args.no_warm
+    ctx = make_ctx(args.path, args.refresh, warm, "chosen")
     res = _timed_steps(ctx, dev, stream, prob.psi_true, K, W, 0, flush, barrier,
                        ClockSampler(local))
     total_ms = max_over_ranks(res["total_ms"])
@@ -419,31 +425,40 @@ def run_ours(args):
     e2e_value = world * K / e2e_s
     ctx.close()
 
-    # plain FP32 path, same workload, same form
-    plain = None
-    if not args.no_plain and args.path != "fp32":
-        pctx = make_ctx("fp32")
-        pres = _timed_steps(pctx, dev, stream, prob.psi_true, K, W, 0, flush, barrier)
-        pprof = _profile_pass(pctx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
-        pctx.close()
-        ptotal = max_over_ranks(pres["total_ms"])
-        pfit = _fit_step_time(pres["step_ms"], pres["rounds"])
-        plain = {"value": world * K / (ptotal / 1000.0), "unit": "steps/s",
-                 "ms_per_step": ptotal / K,
-                 "mvp_rounds_per_step": pres["counters"][0] / K,
-                 "step_time_fit": pfit,
-                 "kv_entry_rhs_per_s": pprof["kv_entry_rhs_per_s"],
-                 "kmv_ms_per_round": (pprof["kmv_ms"] / pprof["rounds"] if pprof["rounds"] else None),
-                 "kernel": KMV_KERNELS["fp32"][0]}
+    # plain FP32 path (probes redrawn every step, cold solves: the method as stated), and
+    # FP32 with the chosen path's method options (isolates the arithmetic), same form
+    def other_leg(path, refresh, warm_leg, key):
+        octx = make_ctx(path, refresh, warm_leg, key)
+        ores = _timed_steps(octx, dev, stream, prob.psi_true, K, W, 0, flush, barrier)
+        oprof = _profile_pass(octx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
+        octx.close()
+        ototal = max_over_ranks(ores["total_ms"])
+        return {"value": world * K / (ototal / 1000.0), "unit": "steps/s",
+                "ms_per_step": ototal / K,
+                "mvp_rounds_per_step": ores["counters"][0] / K,
+                "step_time_fit": _fit_step_time(ores["step_ms"], ores["rounds"]),
+                "kv_entry_rhs_per_s": oprof["kv_entry_rhs_per_s"],
+                "kmv_ms_per_round": (oprof["kmv_ms"] / oprof["rounds"] if oprof["rounds"] else None),
+                "kernel": KMV_KERNELS[path][0], "probe_refresh": refresh,
+                "warm_started_solves": bool(warm_leg)}
+
+    plain = same_method = None
+    if not args.no_plain:
+        plain = other_leg("fp32", 1, False, "plain_fp32")
+        if args.path != "fp32" or warm or args.refresh != 1:
+            same_method = other_leg("fp32", args.refresh, warm, "fp32_same_method")
 
     fit = _fit_step_time(res["step_ms"], res["rounds"])
+    # the arithmetic alone: chosen vs FP32 with the same method options, at the same rounds
     at_equal = None
-    if plain and fit and plain.get("step_time_fit"):
+    ref = same_method or plain
+    if ref and fit and ref.get("step_time_fit"):
         r_bar = rounds / K
         t_c = fit["fixed_ms"] + fit["ms_per_round"] * r_bar
-        t_p = plain["step_time_fit"]["fixed_ms"] + plain["step_time_fit"]["ms_per_round"] * r_bar
+        t_p = ref["step_time_fit"]["fixed_ms"] + ref["step_time_fit"]["ms_per_round"] * r_bar
         at_equal = {"rounds_per_step": r_bar, "chosen_steps_per_s": 1000.0 / t_c,
-                    "plain_fp32_steps_per_s": 1000.0 / t_p, "speedup": t_p / t_c}
+                    "fp32_steps_per_s": 1000.0 / t_p, "speedup": t_p / t_c,
+                    "fp32_leg": "fp32_same_method" if same_method else "plain_fp32"}
     name, traffic_file, _ = KMV_KERNELS[args.path]
     traffic = None
     tf = _kv_file(traffic_file)
@@ -479,11 +494,14 @@ def run_ours(args):
                    "path": ("tcgen05 mixed K V (FP32 kernel values, 3xBF16 contraction)"
                             if args.path == "mixed" else "fp32 SIMT K V"),
                    "step_form": "host loop" if args.no_graph else "one CUDA graph launch per step",
+                   "probe_refresh": args.refresh, "warm_started_solves": warm,
+                   "steps_start_at": "the generating parameters (own step number each)",
                    "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "kv_throughput": {"value": prof["kv_entry_rhs_per_s"], "unit": "entry·RHS/s",
                           "plain_fp32": plain["kv_entry_rhs_per_s"] if plain else None},
         "plain_fp32": plain,
+        "fp32_same_method": same_method,
         "autotune": ({path: {"tuned_over_untuned_ms": [round(e["ms"] / e["ms_default"], 3)
                                                       for e in tab]}
                       for path, tab in tuned.items()} if tuned else None),
