@@ -230,12 +230,14 @@ __global__ void __launch_bounds__(kTcThreads, 3) kmv_tc_kernel(const TcDevArgs a
     const int il = eq * 32 + lane;
     const long long i = row0 + il;
     const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
+    // x^_i pre-scaled by 2 c1, so that the cross-term chain started at a_i + b_j is the
+    // whole exponent: a_i + b_j + 2 c1 x^_i . x^_j
+    const float c0 = a.params->c0f, c1 = a.params->c1f;
+    const float two_c1 = 2.f * c1;
     float xi[DP];
 #pragma unroll
-    for (int k = 0; k < DP; ++k) xi[k] = (i < a.n) ? a.xhat[i * DP + k] : 0.f;
-    const float c0 = a.params->c0f, c1 = a.params->c1f;
+    for (int k = 0; k < DP; ++k) xi[k] = (i < a.n) ? two_c1 * a.xhat[i * DP + k] : 0.f;
     const float ai = c0 + ((i < a.n) ? a.bneg[i] : 0.f);   // log2(sigma^2) - c1 |x^_i|^2
-    const float two_c1 = 2.f * c1;
     bool ok = true;
     int pending = -1;   // tile whose K stores are in flight (signalled one tile late)
     for (int lt = 0; lt < nt; ++lt) {
@@ -248,15 +250,16 @@ __global__ void __launch_bounds__(kTcThreads, 3) kmv_tc_kernel(const TcDevArgs a
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float kk[2];
+        const float2 bj = *reinterpret_cast<const float2*>(tb + half * 16 + 2 * q);
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
           const int j = half * 16 + 2 * q + h2;
           float xj[DP];
           load_row<float, DP>(tx + j * DP, xj);
-          float dot = 0.f;
+          float ex = ai + (h2 == 0 ? bj.x : bj.y);
 #pragma unroll
-          for (int k = 0; k < DP; ++k) dot = fmaf(xi[k], xj[k], dot);
-          kk[h2] = ex2_approx(fminf(fmaf(two_c1, dot, ai + tb[j]), c0));
+          for (int k = 0; k < DP; ++k) ex = fmaf(xi[k], xj[k], ex);
+          kk[h2] = ex2_approx(fminf(ex, c0));
         }
         const __nv_bfloat162 h = __floats2bfloat162_rn(kk[0], kk[1]);
         const float2 hf = __bfloat1622float2(h);
