@@ -552,8 +552,10 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     # the slowest of 576 columns decides a batched step's rounds; a column that has not
     # stopped after max_iter CG iterations is cut off (reported, not fatal)
+    warm = not args.no_warm
     cfg = u.ulisse_config_default(n_probes=8, probe_kind=u.PROBE_RADEMACHER, q=1.0, beta=1.0,
-                                  eps=1e-8, max_iter=3000, seed=20150126 + 1000 * rank)
+                                  eps=1e-8, max_iter=3000, seed=20150126 + 1000 * rank,
+                                  probe_refresh=args.refresh, warm_start_probes=int(warm))
     allow = (u.ULISSE_ERR_MAXITER,)
     cut = [0]
     Xs = [torch.from_numpy(p.X).to(dev) for p in probs]
@@ -600,6 +602,7 @@ def run_batch(args):
                    "n_min": min(p.n for p in probs), "n_max": max(p.n for p in probs),
                    "dims": sorted(set(p.d for p in probs)), "n_probes": 8,
                    "step_form": "host loop" if args.no_graph else "one CUDA graph launch per batched step",
+                   "probe_refresh": args.refresh, "warm_started_solves": warm,
                    "l2": "flushed between timed steps (512 MiB write)"},
         "batched_steps_per_s": K / (total_ms / 1000.0),
         "kv_throughput": {"value": (c1[1] - c0[1]) / (total_ms / 1000.0),

@@ -74,8 +74,7 @@ typedef struct {
                                 -- y always, the probes within a refresh epoch (Sec. 5.1's
                                 reuse of probes and solutions); one extra K V round forms the
                                 initial residuals, and an iterate is kept only when it lowers
-                                the residual (no random draw: the estimates stay unbiased).
-                                Single contexts only. */
+                                the residual (no random draw: the estimates stay unbiased). */
     double q;                /* early-stop threshold alpha = q sqrt(n) (Sec. 4; the paper uses q=1) */
     double beta;             /* ULISSE weights w_r = exp(beta r) (Sec. 4; the paper uses beta=1) */
     double eps;              /* CG convergence threshold on ||e|| (Algorithm 1; paper: 1e-8) */
@@ -331,7 +330,7 @@ ulisse_status ulisse_ws_x0(ulisse_ctx *ctx, const double *psi, int bf16, float *
  * sweep; the work list has one item per (problem, 256-row block), longest rows first.
  * Parameters and gradients are packed: problem b's p_b values follow problem b-1's.
  * Batched contexts run the FP32 path (cfg->precision must be ULISSE_PREC_FP32), take
- * n_probes <= 16, and accept only the ulisse_batch_* calls (plus ulisse_set_graph,
+ * n_probes <= 16 (warm_start_probes applies to every problem), and accept only the ulisse_batch_* calls (plus ulisse_set_graph,
  * counters and destroy); the single-problem calls return ULISSE_ERR_ARG on them.
  *
  *   n_problems  1 .. 4096.   n, d: host arrays of n_problems sizes (1 <= d_b <= 8).

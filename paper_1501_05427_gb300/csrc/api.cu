@@ -115,6 +115,7 @@ struct ulisse_ctx {
   BatchItem* b_items = nullptr;
   int b_n_items = 0;
   BatchKmvDesc* b_kdesc = nullptr;
+  BatchKmvDesc* b_kdesc0 = nullptr;    // warm-started solves: the products K s_0 of all problems
   BatchGradDesc* b_gdesc = nullptr;
   int* b_queue = nullptr;
   int* b_nlive = nullptr;          // device, one live count per problem
@@ -1684,8 +1685,6 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
   if (cfg->precision != ULISSE_PREC_FP32)
     return fail(nullptr, ULISSE_ERR_ARG, "batched contexts run the FP32 path");
   if (cfg->n_probes > 16) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take n_probes <= 16");
-  if (cfg->warm_start_probes)
-    return fail(nullptr, ULISSE_ERR_ARG, "batched contexts do not warm-start their solves");
   for (int b = 0; b < n_problems; ++b)
     if (d[b] < 1 || d[b] > kBatchMaxDP) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take d <= 8");
   ulisse_ctx* ctx = new ulisse_ctx();
@@ -1897,7 +1896,9 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
       sub->prior_zero = true;
     }
   }
+  const bool warm = ctx->cfg.warm_start_probes != 0;
   if (!ctx->b_cgargs) {
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_kdesc0), sizeof(BatchKmvDesc) * B));
     CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_cgargs), sizeof(CgArgs<float>) * B));
     CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_cgprob), sizeof(BatchCgProb) * B));
     CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_rmax), sizeof(int)));
@@ -1913,7 +1914,8 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
   CKS(graph_alloc(ctx));
   std::vector<CgArgs<float>> args(B);
   std::vector<BatchCgProb> probs(B);
-  std::vector<BatchKmvDesc> kd(B);
+  std::vector<BatchKmvDesc> kd(B), kd0(B);
+  const std::vector<int> rcount(B, R);
   std::vector<BatchGradDesc> gd(B);
   int slot0 = 0, maxch = 1;
   for (int b = 0; b < B; ++b) {
@@ -1925,12 +1927,17 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
                                   ((sub->n + kMaxCgChunks - 1) / kMaxCgChunks + 255) / 256 * 256);
     a.nchunk = (int)((sub->n + a.chunk - 1) / a.chunk);
     a.n_live = sub->n_live_dev;
+    if (warm) a.warm_refresh = ctx->cfg.probe_refresh;
     maxch = std::max(maxch, a.nchunk);
     args[b] = a;
     probs[b] = BatchCgProb{sub->st, sub->st_next, sub->live, sub->n_live_dev, R, sub->n};
     kd[b] = BatchKmvDesc{(const float*)sub->xhat, sub->n, sub->DP, 0, sub->params,
                          (const float*)sub->D, sub->ldn, sub->live, (float*)sub->KD, sub->ldn,
                          sub->live, sub->n_live_dev};
+    // K s_0 of warm-started solves: s_0 from Sbest (cap columns after S)
+    kd0[b] = BatchKmvDesc{(const float*)sub->xhat, sub->n, sub->DP, 0, sub->params,
+                          (const float*)sub->S, sub->ldn, sub->warm_map, (float*)sub->KD,
+                          sub->ldn, sub->iota, ctx->b_rcount + b};
     const int nslots = (int)((sub->n + kBatchBM - 1) / kBatchBM);
     gd[b] = BatchGradDesc{(const float*)sub->xhat, sub->n, sub->DP, sub->d, sub->params,
                           (const float*)sub->SE, sub->amap, (const float*)sub->sa_dev,
@@ -1944,6 +1951,10 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
   CK(cudaMemcpyAsync(ctx->b_cgprob, probs.data(), sizeof(BatchCgProb) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_kdesc, kd.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_kdesc0, kd0.data(), sizeof(BatchKmvDesc) * B, cudaMemcpyHostToDevice,
+                     ctx->stream));
+  CK(cudaMemcpyAsync(ctx->b_rcount, rcount.data(), sizeof(int) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_gdesc, gd.data(), sizeof(BatchGradDesc) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
@@ -1973,8 +1984,19 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
     probes_kernel<float><<<pg, 256, 0, ctx->stream>>>((float*)sub->B, sub->ldn, sub->n, nr,
                                                       ctx->cfg.probe_kind, sub->cfg.seed, 0,
                                                       ctx->chain, ctx->cfg.probe_refresh);
+  }
+  CK(cudaGetLastError());
+  // warm-started solves: every problem's K s_0 in one persistent launch, then the starts
+  const bool warm = ctx->cfg.warm_start_probes != 0;
+  if (warm)
+    CK(launch_kmv_batch(ctx->b_kdesc0, ctx->b_items, ctx->b_n_items, ctx->b_queue,
+                        kBatchWidths[batch_width_bucket(R)], ctx->num_sms, ctx->status_dev,
+                        ctx->stream));
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
     CgArgs<float> a = cg_args<float>(sub, 0, 0);
     a.cs = ctx->chain;
+    if (warm) a.warm_refresh = ctx->cfg.probe_refresh;
     cg_init_kernel<float><<<R, kCgNT, 0, ctx->stream>>>(a);
     CK(cudaMemsetAsync(sub->n_live_dev, 0, sizeof(int), ctx->stream));
   }
@@ -2060,9 +2082,11 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
     }
   }
   // the second estimate of K^{-1} y as the right factor; the gradient sweep
-  for (ulisse_ctx* sub : ctx->subs)
+  for (ulisse_ctx* sub : ctx->subs) {
+    if (warm) CK(cudaMemsetAsync(sub->warm_valid, 0x01, sizeof(int), ctx->stream));
     CK(cudaMemcpyAsync(sub->B, (char*)sub->SE + sub->ldn * 4, sub->ldn * 4,
                        cudaMemcpyDeviceToDevice, ctx->stream));
+  }
   CK(launch_grad_batch(ctx->b_gdesc, B, ctx->b_items, ctx->b_n_items, ctx->b_queue, ctx->b_gpart,
                        R, ctx->num_sms, ctx->status_dev, ctx->stream));
   if (sgld) {
@@ -2093,10 +2117,12 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
 static void batch_count_fixed(ulisse_ctx* ctx, int steps, bool sgld) {
   const int B = (int)ctx->subs.size();
   const int R = 1 + ctx->cfg.n_probes;
+  const bool warm = ctx->cfg.warm_start_probes != 0;
   double ent = 0.0;
   for (ulisse_ctx* sub : ctx->subs) ent += (double)sub->n * (double)sub->n * R;
-  ctx->launches += (long long)steps * (3LL * B + 2 + (sgld ? B + 1 : 0));
-  ctx->entry_rhs += steps * ent;
+  ctx->launches += (long long)steps * (3LL * B + 2 + (sgld ? B + 1 : 0) + (warm ? 1 : 0));
+  ctx->entry_rhs += steps * ent * (warm ? 2.0 : 1.0);
+  if (warm) ctx->mvp_rounds += steps;
 }
 
 static ulisse_status batch_fold_gstat(ulisse_ctx* ctx) {
@@ -2421,6 +2447,7 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   dev_free(reinterpret_cast<void*&>(ctx->eps_one));
   if (ctx->h_gstat) cudaFreeHost(ctx->h_gstat);
   for (void** p : {reinterpret_cast<void**>(&ctx->b_cgargs), reinterpret_cast<void**>(&ctx->b_cgprob),
+                   reinterpret_cast<void**>(&ctx->b_kdesc0),
                    reinterpret_cast<void**>(&ctx->b_rmax), reinterpret_cast<void**>(&ctx->b_psi)})
     dev_free(*p);
   if (ctx->b_h_rmax) cudaFreeHost(ctx->b_h_rmax);

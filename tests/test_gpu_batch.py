@@ -236,3 +236,35 @@ def test_batch_graph_uneven_workload():
             traces.append(tr.cpu().numpy())
     assert np.all(np.isfinite(traces[0]))
     assert np.array_equal(traces[0], traces[1])
+
+
+def test_batch_warm_solves_graph_and_single_contexts():
+    """Warm-started solves in a batch: the graph chain equals the host loop bit for bit, and
+    over consecutive gradient steps each problem follows a warm-started single context with
+    seed cfg.seed + b (same integer decisions, gradients within FP32 rounding)."""
+    spec = [(1800, 8), (900, 4), (2600, 2)]
+    probs = [w.census_like(n=n, d=d, seed=5000 + n) for n, d in spec]
+    psi0 = np.concatenate([p.psi_true for p in probs])
+    cfg = dict(n_probes=8, seed=21, probe_refresh=3, warm_start_probes=1)
+    traces = []
+    for graph in (False, True):
+        # a fresh batch each time: the warm starts carry state from step to step
+        with _batch(probs, **cfg) as bc:
+            bc.set_graph(graph)
+            psi = torch.tensor(psi0, dtype=torch.float64, device="cuda")
+            eps = torch.full((5,), 1e-3, dtype=torch.float64, device="cuda")
+            tr = torch.zeros((5, bc.n_params), dtype=torch.float64, device="cuda")
+            bc.sgld_chain(psi, eps, step0=7, trace_dev=tr)
+            traces.append(tr.cpu().numpy())
+    assert np.array_equal(traces[0], traces[1])
+    with _batch(probs, **cfg) as bc:
+        out_b = [bc.grad(psi0, step=s) for s in range(4)]
+    for b, p in enumerate(probs):
+        X = torch.from_numpy(p.X).cuda()
+        y = torch.from_numpy(p.y).cuda()
+        c = dict(cfg, seed=cfg["seed"] + b)
+        with u.Context(X, y, u.ulisse_config_default(**c)) as ctx:
+            out_s = [ctx.grad(p.psi_true, step=s) for s in range(4)]
+        for (gb, stb), (gs, sts) in zip(out_b, out_s):
+            assert [tuple(s[:4]) for s in sts] == [tuple(s[:4]) for s in stb[b]]
+            assert np.linalg.norm(bc.split(gb)[b] - gs) <= 1e-4 * np.linalg.norm(gs)
