@@ -193,10 +193,38 @@ ulisse_status ulisse_solve(ulisse_ctx *ctx, const double *psi, const float *B, i
  * the ULISSE estimate of K^{-1} r_j, and probes r_j drawn for epoch step / probe_refresh
  * (probe column j >= 1, element i from Philox counter (i, j, epoch, 1)).
  *   psi   host, p doubles.   g  host, p doubles (output).   stats: host, 1 + N_r, or NULL.
- * Synchronises the stream.
+ * The sums over covariance entries are the fused pass of ulisse_dk_bilinear (same precision
+ * rules).  Synchronises the stream.
  */
 ulisse_status ulisse_grad(ulisse_ctx *ctx, const double *psi, unsigned long long step,
                           double *g, ulisse_col_stats *stats);
+
+/*
+ * The fused gradient pass on its own (Eq. gradient:unbiased, Sec. 4.1): for every parameter
+ * i = 0..d+1 (psi order: log l_1..log l_d, log sigma^2, log lambda),
+ *     out[i] = sum_{m < M} scale[m] a_m^T (dK/dpsi_i) b_m,
+ * dK/dpsi_i the covariance derivatives of ulisse_kmv (which = i).  One sweep over generated
+ * covariance tiles gives all d + 2 components: with W_ab = sum_m scale[m] a_m[a] b_m[b],
+ *     out[log l_k] = sum_ab k_s(a,b) W_ab (x_ak - x_bk)^2 / l_k^2,
+ *     out[log sigma^2] = sum_ab k_s(a,b) W_ab,   out[log lambda] = lambda sum_a W_aa.
+ * ulisse_grad evaluates this form with the solver's estimates and the probes as factors.
+ *   psi    host, d + 2 doubles.
+ *   A, B   device, n x M column-major float (leading dimension n), 1 <= M <= 64; read only.
+ *   scale  host, M doubles, or NULL for all ones.
+ *   out    host, d + 2 doubles (output).  Synchronises the context's stream.
+ * Precision: FP32 contexts sum each tile in FP32 and the tiles in FP64; FP64 contexts convert
+ * A and B to double and compute in FP64; mixed contexts run the pass on the tensor cores:
+ * W = A B^T and the sums [S | G | H] = P [x, x^2, 1] of P = k_s o W by three BF16 products
+ * each (high/low split) with FP32 accumulation, then out[log l_k] = sum_a x_ak^2 S_a -
+ * 2 x_ak G_ak + H_ak in FP64 (x = x / l): each component within about 1e-4 of the scale
+ * sum_m |scale[m]| |a_m|^T |dK/dpsi_i| |b_m|.
+ * Works in the context's right-hand-side and estimate buffers, which every solve and gradient
+ * call rewrites; the iterates kept for warm-started solves are not touched.
+ * Errors: ULISSE_ERR_ARG (null, M out of range, non-finite psi or scale, batched context),
+ * ULISSE_ERR_CUDA, ULISSE_ERR_TIMEOUT.
+ */
+ulisse_status ulisse_dk_bilinear(ulisse_ctx *ctx, const double *psi, const float *A,
+                                 const float *B, int M, const double *scale, double *out);
 
 /*
  * One SGLD step (Sec. 2.1) on psi:

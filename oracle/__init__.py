@@ -222,6 +222,21 @@ def dkmv_all(X, psi, V):
     return np.transpose(U, (0, 2, 1)).copy()
 
 
+def dk_bilinear(X, psi, A, B, scale=None):
+    """out_i = sum_m scale_m a_m^T (dK/dpsi_i) b_m for all p parameters: the bilinear forms
+    the gradient estimate (Eq. gradient:unbiased) is assembled from.  A, B: (n, M).  The
+    derivative products dK/dpsi_i b_m come from dkmv_all; the rest is a plain sum."""
+    A = _f64(A)
+    B = _f64(B)
+    if A.ndim == 1:
+        A = A[:, None]
+        B = B[:, None]
+    M = A.shape[1]
+    s = np.ones(M) if scale is None else _f64(scale)
+    U = dkmv_all(X, psi, B)                      # (p, n, M)
+    return np.einsum("jm,ijm,m->i", A, U, s)
+
+
 # ----------------------------------------------------------------------------------------
 # CG (Algorithm 1) and ULISSE (Sec. 4)
 # ----------------------------------------------------------------------------------------

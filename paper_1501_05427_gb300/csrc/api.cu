@@ -27,6 +27,7 @@ struct ulisse_ctx {
   long long ld128 = 0;        // rows of the tensor-core operand images (multiple of 128)
   float* bneg = nullptr;      // -log2(e)/2 |x^|^2 per input (tensor-core path)
   void *Vt_hi = nullptr, *Vt_lo = nullptr;
+  void *Gt_hi = nullptr, *Gt_lo = nullptr;   // packed operands of the tensor-core gradient
 
   float* X = nullptr;         // raw inputs, n x d row-major
   void* y = nullptr;          // labels, ldn (element type T)
@@ -59,6 +60,8 @@ struct ulisse_ctx {
   int* amap = nullptr;        // gradient left-factor columns
   int* bmap = nullptr;        // gradient right-factor columns
   int grad_nr = -1;           // probe count the maps were built for
+  int* q_map = nullptr;       // ulisse_dk_bilinear: identity column map (kMaxM)
+  void* q_sa = nullptr;       // ulisse_dk_bilinear: scales (T), kMaxM
 
   double* M_dev = nullptr;
   double* prior_dev = nullptr;
@@ -617,7 +620,10 @@ static ulisse_status ensure_grad_maps(ulisse_ctx* ctx, int nr) {
   return ULISSE_OK;
 }
 
-static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
+// The fused gradient pass over the columns of SE (left factors, scaled) and B (right factors);
+// the maps and scales default to the gradient's own.
+static ulisse_status run_grad(ulisse_ctx* ctx, int M, const int* amap = nullptr,
+                              const void* sa = nullptr, const int* bmap = nullptr) {
   GradLaunch L{};
   L.xhat = ctx->xhat;
   L.n = ctx->n;
@@ -625,10 +631,10 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
   L.d = ctx->d;
   L.DP = ctx->DP;
   L.A = ctx->SE;
-  L.amap = ctx->amap;
-  L.sa = ctx->sa_dev;
+  L.amap = amap ? amap : ctx->amap;
+  L.sa = sa ? sa : ctx->sa_dev;
   L.B = ctx->B;
-  L.bmap = ctx->bmap;
+  L.bmap = bmap ? bmap : ctx->bmap;
   L.ld = ctx->ldn;
   L.M = M;
   L.params = ctx->params;
@@ -636,13 +642,19 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
   L.g_out = ctx->g_dev;
   L.status = ctx->status_dev;
   L.num_sms = ctx->num_sms;
+  L.bneg = ctx->bneg;
+  L.tc_hi = ctx->Gt_hi;
+  L.tc_lo = ctx->Gt_lo;
+  L.tc_ld = ctx->ld128;
   for (int attempt = 0; attempt < 2; ++attempt) {
     L.partials = ctx->gpart;
     L.partials_len = ctx->gpart_len;
     L.plan_only = ctx->planning;
     cudaEvent_t ea = nullptr, eb = nullptr;
     prof_begin(ctx, &ea, &eb);
-    cudaError_t e = ctx->f64 ? launch_grad_f64(L, ctx->stream) : launch_grad_f32(L, ctx->stream);
+    cudaError_t e = ctx->f64     ? launch_grad_f64(L, ctx->stream)
+                    : ctx->mixed ? launch_grad_tc(L, ctx->stream)
+                                 : launch_grad_f32(L, ctx->stream);
     if (ctx->prof) {
       if (e == cudaSuccess && !ctx->planning)
         prof_end(ctx, 1, ea, eb, (double)ctx->n * ctx->n * (5.0 * ctx->d + 4.0 + 2.0 * M));
@@ -650,7 +662,7 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M) {
         ctx->free_events.push_back({ea, eb});
     }
     if (e == cudaSuccess && !ctx->planning) {
-      if (!ctx->capturing) ctx->launches++;
+      if (!ctx->capturing) ctx->launches += ctx->mixed ? 3 : 1;   // tensor cores: 2 packings
       break;
     }
     if (e != cudaSuccess && (e != cudaErrorMemoryAllocation || attempt == 1 || ctx->capturing))
@@ -799,7 +811,9 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
   if (ctx->mixed) {
     if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bneg), sizeof(float) * ctx->ld128)) ||
         (s = dev_alloc(ctx, &ctx->Vt_hi, 2 * ctx->ld128 * 64)) ||
-        (s = dev_alloc(ctx, &ctx->Vt_lo, 2 * ctx->ld128 * 64)))
+        (s = dev_alloc(ctx, &ctx->Vt_lo, 2 * ctx->ld128 * 64)) ||
+        (s = dev_alloc(ctx, &ctx->Gt_hi, 2 * ctx->ld128 * 112)) ||
+        (s = dev_alloc(ctx, &ctx->Gt_lo, 2 * ctx->ld128 * 112)))
       return bail(s);
   }
   if (cudaMallocHost(&ctx->h_n_live, sizeof(int)) != cudaSuccess ||
@@ -998,6 +1012,59 @@ ulisse_status ulisse_grad(ulisse_ctx* ctx, const double* psi, unsigned long long
   CK(cudaMemcpyAsync(g, ctx->g_dev, sizeof(double) * (ctx->d + 2), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CKS(copy_stats(ctx, stats, 1 + ctx->cfg.n_probes));
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+ulisse_status ulisse_dk_bilinear(ulisse_ctx* ctx, const double* psi, const float* A,
+                                 const float* B, int M, const double* scale, double* out) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: not supported");
+  if (!A || !B || !out || M < 1 || M > kMaxM)
+    return fail(ctx, ULISSE_ERR_ARG, "A/B/out null or M out of range");
+  if (scale)
+    for (int m = 0; m < M; ++m)
+      if (!std::isfinite(scale[m])) return fail(ctx, ULISSE_ERR_ARG, "scale not finite");
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  CKS(ensure_columns(ctx, M, M));
+  if (!ctx->q_map) {
+    std::vector<int> id(kMaxM);
+    for (int m = 0; m < kMaxM; ++m) id[m] = m;
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->q_map), sizeof(int) * kMaxM));
+    CKS(dev_alloc(ctx, &ctx->q_sa, sizeof(double) * kMaxM));
+    CK(cudaMemcpy(ctx->q_map, id.data(), sizeof(int) * kMaxM, cudaMemcpyHostToDevice));
+  }
+  CK(cudaStreamSynchronize(ctx->stream));   // the scale upload below reuses a host buffer
+  std::vector<double> sd(M, 1.0);
+  std::vector<float> sf(M, 1.f);
+  for (int m = 0; m < M; ++m) {
+    if (scale) sd[m] = scale[m];
+    sf[m] = (float)sd[m];
+  }
+  if (ctx->f64)
+    CK(cudaMemcpy(ctx->q_sa, sd.data(), sizeof(double) * M, cudaMemcpyHostToDevice));
+  else
+    CK(cudaMemcpy(ctx->q_sa, sf.data(), sizeof(float) * M, cudaMemcpyHostToDevice));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  const long long n = ctx->n;
+  auto in_cols = [&](const float* src, void* dst) -> ulisse_status {
+    if (!ctx->f64) {
+      CK(cudaMemcpy2DAsync(dst, ctx->ldn * 4, src, n * 4, n * 4, M, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    } else {
+      convert_cols_kernel<float, double><<<dim3(64, M), 256, 0, ctx->stream>>>(
+          src, n, (double*)dst, ctx->ldn, n);
+      CK(cudaGetLastError());
+    }
+    return ULISSE_OK;
+  };
+  CKS(in_cols(A, ctx->SE));
+  CKS(in_cols(B, ctx->B));
+  CKS(run_grad(ctx, M, ctx->q_map, ctx->q_sa, ctx->q_map));
+  CK(cudaMemcpyAsync(out, ctx->g_dev, sizeof(double) * (ctx->d + 2), cudaMemcpyDeviceToHost,
+                     ctx->stream));
   int st = 0;
   CKS(read_status(ctx, &st));
   return status_to_result(ctx, st);
@@ -1280,7 +1347,8 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
   // what one launch does outside the CG loop (the loop's share is counted on the device)
   const long long kmv_per = ctx->mixed ? 2 : 1, kmv_cols = ctx->mixed ? 64 : kMaxRChunk;
   const int init_cols = warm ? R : s0_cols;   // columns of the product K s_0
-  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + 1 + 1 + (s0_cols > 0 ? 2 : 0) +
+  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + (ctx->mixed ? 3 : 1) + 1 +
+      (s0_cols > 0 ? 2 : 0) +
       (init_cols > 0 ? kmv_per * ((init_cols + kmv_cols - 1) / kmv_cols) : 0);
   ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + init_cols);
   ctx->graph_rounds_fixed = init_cols > 0 ? 1 : 0;
@@ -2420,7 +2488,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   for (void** p : {reinterpret_cast<void**>(&ctx->st_next), reinterpret_cast<void**>(&ctx->part1),
                    reinterpret_cast<void**>(&ctx->part2), reinterpret_cast<void**>(&ctx->bneg),
-                   &ctx->Vt_hi, &ctx->Vt_lo})
+                   &ctx->Vt_hi, &ctx->Vt_lo, &ctx->Gt_hi, &ctx->Gt_lo,
+                   reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa})
     dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,
                    reinterpret_cast<void**>(&ctx->params), reinterpret_cast<void**>(&ctx->psi_dev),

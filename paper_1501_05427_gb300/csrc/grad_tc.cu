@@ -1,0 +1,525 @@
+// Mixed-precision fused gradient pass on the 5th-generation tensor cores (Eq. gradient:unbiased,
+// Sec. 4.1): the components of
+//     g~_i = sum_m a_m^T dK_i b_m
+// for all parameters at once, through W_ij = sum_m a_m[i] b_m[j] and P_ij = k_s(i,j) W_ij:
+//     g~_{log l_k}     = sum_ij P_ij (x^_ik - x^_jk)^2
+//                      = sum_i [ x^_ik^2 S_i - 2 x^_ik G_ik + H_ik ],
+//                        S_i = sum_j P_ij,  G_ik = sum_j P_ij x^_jk,  H_ik = sum_j P_ij x^_jk^2
+//     g~_{log sigma^2} = sum_i S_i
+//     g~_{log lambda}  = lambda sum_i W_ii.
+// For a block of 128 rows I and each 32-point tile J:
+//   1. W_IJ = A^_I B^_J^T on the tensor cores (K = the factor index m, A^ = scaled a-columns,
+//      both split into BF16 high + low parts: three products), into tensor memory;
+//   2. the epilogue warps read W back (tcgen05.ld), form the kernel values as the K V kernel
+//      does (cross term from row norms, one ex2), multiply, split P into BF16 high + low parts
+//      and store them over W's own tensor-memory columns;
+//   3. [S | G | H]_I += P_IJ Z_J on the tensor cores, Z_j = [x^_j, x^_j^2, 1] split the same
+//      way, accumulated in tensor memory across all tiles of the CTA's j range.
+// The per-row combination and the diagonal sum run in FP64 at the end; CTA partials are summed
+// in a fixed order by the last CTA to arrive (as in the SIMT gradient kernel).  Warp 0 streams
+// x^_J, the row norms, B^_J and Z_J into a 4-stage ring with bulk copies; one thread of warp 1
+// issues the MMAs; eight epilogue warps (a tensor-memory lane quadrant and half of the tile's
+// 32 columns each) make P.  W/P tiles are double-buffered; a buffer is refilled only after the
+// MMAs that read it have completed.  Every wait is bounded.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kmv_kernel.cuh"
+#include "tc_common.cuh"
+
+namespace ulisse {
+
+constexpr int kGtBN = 32;
+constexpr int kGtBM = 128;
+constexpr int kGtThreads = 320;    // warp 0 producer, warp 1 MMA issuer, warps 2-9 epilogue
+constexpr uint32_t kGtCols = 128;  // tensor-memory columns per CTA
+constexpr int kGtZOff = 64;        // Z image offset in the packed scratch, in units of ld128
+
+__device__ inline void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(v);
+  l = __float2bfloat16_rn(v - __bfloat162float(h));
+}
+
+// Right factors b_m (m < M) of every 32-point tile as BF16 high and low parts: a K-major
+// canonical image of 32 points (rows) x K1 factors; factors m >= M and points j >= n are zero.
+__global__ void pack_bt_kernel(const float* __restrict__ B, long long ld,
+                               const int* __restrict__ bmap, int M, int K1, long long n,
+                               long long ntiles, __nv_bfloat16* __restrict__ Bhi,
+                               __nv_bfloat16* __restrict__ Blo) {
+  const long long per_tile = (long long)kGtBN * K1;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntiles * per_tile;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long t = idx / per_tile;
+    const int rem = (int)(idx - t * per_tile);
+    const int m = rem / kGtBN, j = rem - m * kGtBN;
+    const long long jj = t * kGtBN + j;
+    const float v = (m < M && jj < n) ? B[(long long)bmap[m] * ld + jj] : 0.f;
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    const long long off = t * per_tile + tc::canon_offset(j, m, 2, K1 / 8) / 2;
+    Bhi[off] = h;
+    Blo[off] = l;
+  }
+}
+
+// Z_j = [x^_j (DP), x^_j^2 (DP), 1, 0...] for every tile as BF16 high and low parts: a
+// K-major canonical image of N2 rows (accumulator columns) x 32 points; points j >= n are zero.
+__global__ void pack_z_kernel(const float* __restrict__ xhat, int DP, long long n, int N2,
+                              long long ntiles, __nv_bfloat16* __restrict__ Zhi,
+                              __nv_bfloat16* __restrict__ Zlo) {
+  const long long per_tile = (long long)N2 * kGtBN;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntiles * per_tile;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long t = idx / per_tile;
+    const int rem = (int)(idx - t * per_tile);
+    const int c = rem / kGtBN, j = rem - c * kGtBN;
+    const long long jj = t * kGtBN + j;
+    float v = 0.f;
+    if (jj < n) {
+      if (c < DP) {
+        v = xhat[jj * DP + c];
+      } else if (c < 2 * DP) {
+        const float x = xhat[jj * DP + (c - DP)];
+        v = x * x;
+      } else if (c == 2 * DP) {
+        v = 1.f;
+      }
+    }
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    const long long off = t * per_tile + tc::canon_offset(c, j, 2, kGtBN / 8) / 2;
+    Zhi[off] = h;
+    Zlo[off] = l;
+  }
+}
+
+struct GtDevArgs {
+  const float* xhat;   // x^ rows (ld x DP, row-major)
+  const float* bneg;   // -c1 |x^|^2
+  const __nv_bfloat16* Bt_hi;
+  const __nv_bfloat16* Bt_lo;
+  const __nv_bfloat16* Zt_hi;
+  const __nv_bfloat16* Zt_lo;
+  const float* A;      // left factors: column amap[m], scaled by sa[m]
+  const int* amap;
+  const float* sa;
+  const float* B;      // right factors (the diagonal term reads them unsplit)
+  const int* bmap;
+  long long ld;
+  int M;
+  long long n;
+  int d;
+  const DevParams* params;
+  int nsplit, tiles_per_split, ntiles;
+  double* partials;
+  int* counter;
+  double* g_out;
+  int* status;
+};
+
+template <int DP, int KS>
+struct GtShape {
+  static constexpr int K1 = 16 * KS;                   // factor dimension, padded
+  static constexpr int N2 = (2 * DP + 1 + 15) / 16 * 16;
+  static constexpr int ST = 4;
+  static constexpr uint32_t A_BYTES = kGtBM * K1 * 2;  // one part of A^_I
+  static constexpr uint32_t X_BYTES = kGtBN * DP * 4;
+  static constexpr uint32_t BN_BYTES = kGtBN * 4;
+  static constexpr uint32_t BT_BYTES = kGtBN * K1 * 2;
+  static constexpr uint32_t Z_BYTES = N2 * kGtBN * 2;
+  static constexpr uint32_t STAGE_BYTES = X_BYTES + BN_BYTES + 2 * BT_BYTES + 2 * Z_BYTES;
+  static constexpr uint32_t OFF_STAGES = 2 * A_BYTES;
+  static constexpr uint32_t OFF_BARS = OFF_STAGES + ST * STAGE_BYTES;
+  static constexpr int NBARS = 2 * ST + 2 + 2 + 2 + 1;  // full, empty, w_full, p_full, free, done
+  static constexpr uint32_t SMEM = OFF_BARS + NBARS * 8 + 64;
+  // tensor-memory columns: two W/P buffers of 32, then the [G | H | S] accumulator
+  static constexpr uint32_t COL_D2 = 64;
+  static_assert(COL_D2 + N2 <= kGtCols, "tensor memory layout exceeds the allocation");
+  static_assert(X_BYTES % 16 == 0 && STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0,
+                "bulk copies and descriptors need 16-byte alignment");
+};
+
+__device__ inline bool gt_warp_wait(uint64_t* bar, uint32_t parity) {
+  const bool ok = mbar_wait_spin(bar, parity);
+  return __all_sync(0xffffffffu, ok);
+}
+
+template <int DP, int KS>
+__global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(const GtDevArgs a) {
+  using S = GtShape<DP, KS>;
+  constexpr int ST = S::ST, K1 = S::K1, N2 = S::N2;
+  constexpr int NACC = DP + 2;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ double s_red[8][NACC];
+  unsigned char* sAh = smem;
+  unsigned char* sAl = smem + S::A_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BARS);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + ST;
+  uint64_t* w_full = bars + 2 * ST;
+  uint64_t* p_full = w_full + 2;
+  uint64_t* b_free = p_full + 2;
+  uint64_t* done = b_free + 2;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + S::OFF_BARS + S::NBARS * 8);
+  volatile int* s_fail = reinterpret_cast<volatile int*>(s_tmem + 1);
+  int* s_last = reinterpret_cast<int*>(s_tmem + 2);
+  auto stage = [&](int s) -> unsigned char* { return smem + S::OFF_STAGES + s * S::STAGE_BYTES; };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int rb = blockIdx.x / a.nsplit;
+  const int sp = blockIdx.x - rb * a.nsplit;
+  const long long row0 = (long long)rb * kGtBM;
+  const int tile_begin = sp * a.tiles_per_split;
+  const int nt = max(0, min(tile_begin + a.tiles_per_split, a.ntiles) - tile_begin);
+
+  // A^_I = sa[m] a_m[i], split into BF16 high and low parts (K-major canonical image).
+  for (int idx = tid; idx < kGtBM * K1; idx += kGtThreads) {
+    const int m = idx / kGtBM, il = idx - m * kGtBM;
+    const long long i = row0 + il;
+    const float v = (m < a.M && i < a.n) ? a.sa[m] * a.A[(long long)a.amap[m] * a.ld + i] : 0.f;
+    __nv_bfloat16 h, l;
+    split_bf16(v, h, l);
+    const uint32_t off = tc::canon_offset(il, m, 2, K1 / 8);
+    *reinterpret_cast<__nv_bfloat16*>(sAh + off) = h;
+    *reinterpret_cast<__nv_bfloat16*>(sAl + off) = l;
+  }
+  tc::fence_async_smem();
+  if (tid == 0) {
+    for (int s = 0; s < ST; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1 + 8);   // MMA commit + the eight epilogue warps
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&w_full[b], 1);
+      mbar_init(&p_full[b], 8);
+      mbar_init(&b_free[b], 1);
+    }
+    mbar_init(done, 1);
+    fence_barrier_init();
+    *s_fail = 0;
+  }
+  if (warp == 1) tc::tmem_alloc(s_tmem, kGtCols);
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tbase = *s_tmem;
+
+  double acc[NACC];
+#pragma unroll
+  for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
+
+  if (warp == 0) {
+    // ------------- producer: x^_J, b_J, B^_J and Z_J tiles into the ring -------------
+    if (lane == 0) {
+      for (int lt = 0; lt < nt; ++lt) {
+        const int s = lt % ST;
+        if (lt >= ST && !mbar_wait_spin(&empty[s], (uint32_t)(((lt / ST) - 1) & 1))) {
+          *s_fail = 1;
+          break;
+        }
+        if (*s_fail) break;
+        const long long t = tile_begin + lt;
+        unsigned char* st = stage(s);
+        mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+        bulk_g2s(st, a.xhat + t * kGtBN * DP, S::X_BYTES, &full[s]);
+        bulk_g2s(st + S::X_BYTES, a.bneg + t * kGtBN, S::BN_BYTES, &full[s]);
+        unsigned char* bt = st + S::X_BYTES + S::BN_BYTES;
+        bulk_g2s(bt, a.Bt_hi + t * kGtBN * K1, S::BT_BYTES, &full[s]);
+        bulk_g2s(bt + S::BT_BYTES, a.Bt_lo + t * kGtBN * K1, S::BT_BYTES, &full[s]);
+        bulk_g2s(bt + 2 * S::BT_BYTES, a.Zt_hi + t * N2 * kGtBN, S::Z_BYTES, &full[s]);
+        bulk_g2s(bt + 2 * S::BT_BYTES + S::Z_BYTES, a.Zt_lo + t * N2 * kGtBN, S::Z_BYTES,
+                 &full[s]);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------- MMA issuer: W = A^ B^T, then [G | H | S] += P Z -------------
+    if (lane == 0) {
+      constexpr uint32_t idesc_w = tc::instr_desc(1, kGtBM, kGtBN);
+      constexpr uint32_t idesc_g = tc::instr_desc(1, kGtBM, N2);
+      constexpr uint32_t sbo_k1 = (K1 / 8) * 128;
+      const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl);
+      auto issue_w = [&](int p) -> bool {
+        const int s = p % ST, b = p & 1;
+        if (!mbar_wait_spin(&full[s], (uint32_t)((p / ST) & 1))) return false;
+        tc::fence_after();
+        const uint32_t bH = smem_u32(stage(s) + S::X_BYTES + S::BN_BYTES);
+        const uint32_t bL = bH + S::BT_BYTES;
+        const uint32_t dW = tbase + (uint32_t)(b * 32);
+#pragma unroll
+        for (int term = 0; term < 3; ++term) {
+          const uint32_t A = term == 2 ? aL : aH;
+          const uint32_t B = term == 1 ? bL : bH;
+#pragma unroll
+          for (int ks = 0; ks < KS; ++ks)
+            tc::mma_bf16(dW, tc::smem_desc(A + ks * 256, 128, sbo_k1),
+                         tc::smem_desc(B + ks * 256, 128, sbo_k1), idesc_w, (term | ks) != 0);
+        }
+        tc::commit(&w_full[b]);
+        return true;
+      };
+      bool ok = true;
+      for (int p = 0; p < min(2, nt) && ok; ++p) ok = issue_w(p);
+      for (int p = 0; p < nt && ok; ++p) {
+        if (*s_fail) { ok = false; break; }
+        const int s = p % ST, b = p & 1;
+        if (!mbar_wait_spin(&p_full[b], (uint32_t)((p / 2) & 1))) { ok = false; break; }
+        tc::fence_after();
+        const uint32_t zH = smem_u32(stage(s) + S::X_BYTES + S::BN_BYTES + 2 * S::BT_BYTES);
+        const uint32_t zL = zH + S::Z_BYTES;
+        const uint32_t pcol = tbase + (uint32_t)(b * 32);
+#pragma unroll
+        for (int term = 0; term < 3; ++term) {
+          const uint32_t A = pcol + (term == 2 ? 8u : 0u);   // P high | P low per 16 points
+          const uint32_t B = term == 1 ? zL : zH;
+#pragma unroll
+          for (int ks = 0; ks < kGtBN / 16; ++ks)
+            tc::mma_bf16_ts(tbase + S::COL_D2, A + ks * 16, tc::smem_desc(B + ks * 256, 128, 512),
+                            idesc_g, (p | term | ks) != 0);
+        }
+        tc::commit(&empty[s]);
+        if (p + 2 < nt) {
+          // buffer b is rewritten by tile p + 2's W only after these MMAs have read P
+          tc::commit(&b_free[b]);
+          if (!mbar_wait_spin(&b_free[b], (uint32_t)((p / 2) & 1))) { ok = false; break; }
+          tc::fence_after();
+          ok = issue_w(p + 2);
+        }
+      }
+      if (!ok) *s_fail = 1;
+      tc::commit(done);
+    }
+  } else {
+    // ------------- epilogue: 8 warps, (lane quadrant, column half) each -------------
+    const int eq = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const int il = eq * 32 + lane;
+    const long long i = row0 + il;
+    const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
+    const float c0 = a.params->c0f, c1 = a.params->c1f;
+    const float two_c1 = 2.f * c1;
+    float xi[DP];
+#pragma unroll
+    for (int k = 0; k < DP; ++k) xi[k] = (i < a.n) ? two_c1 * a.xhat[i * DP + k] : 0.f;
+    const float ai = c0 + ((i < a.n) ? a.bneg[i] : 0.f);
+    bool ok = true;
+    for (int lt = 0; lt < nt; ++lt) {
+      const int s = lt % ST, b = lt & 1;
+      const bool ready = gt_warp_wait(&full[s], (uint32_t)((lt / ST) & 1)) &&
+                         gt_warp_wait(&w_full[b], (uint32_t)((lt / 2) & 1));
+      if (!__all_sync(0xffffffffu, ready && !*s_fail)) { ok = false; break; }
+      tc::fence_after();
+      const uint32_t wcol = tbase + lane_base + (uint32_t)(b * 32 + half * 16);
+      float w[16];
+      tc::tmem_ld16(wcol, w);
+      const float* tx = reinterpret_cast<const float*>(stage(s));
+      const float* tb = reinterpret_cast<const float*>(stage(s) + S::X_BYTES);
+      uint32_t hi[8], lo[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        float pk[2];
+        const float2 bj = *reinterpret_cast<const float2*>(tb + half * 16 + 2 * q);
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int j = half * 16 + 2 * q + h2;
+          float xj[DP];
+          load_row<float, DP>(tx + j * DP, xj);
+          float ex = ai + (h2 == 0 ? bj.x : bj.y);
+#pragma unroll
+          for (int k = 0; k < DP; ++k) ex = fmaf(xi[k], xj[k], ex);
+          pk[h2] = ex2_approx(fminf(ex, c0)) * w[2 * q + h2];
+        }
+        const __nv_bfloat162 h = __floats2bfloat162_rn(pk[0], pk[1]);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(pk[0] - hf.x, pk[1] - hf.y);
+        hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+        lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+      }
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&empty[s]);   // x^_J and b_J consumed
+      // P over this warp's own 16 W columns: high parts first, then low parts
+      tc::tmem_st8(wcol, hi);
+      tc::tmem_st8(wcol + 8, lo);
+      tc::tmem_wait_st();
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&p_full[b]);
+    }
+    if (!ok) *s_fail = 1;
+    const bool fin = ok && gt_warp_wait(done, 0);
+    ok = __all_sync(0xffffffffu, fin && !*s_fail);
+    if (ok && nt > 0) {
+      tc::fence_after();
+      if (half == 0) {
+        float g[N2];
+#pragma unroll
+        for (int c = 0; c < N2 / 16; ++c) {
+          float v[16];
+          tc::tmem_ld16(tbase + lane_base + S::COL_D2 + (uint32_t)(c * 16), v);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) g[c * 16 + q] = v[q];
+        }
+        if (i < a.n) {
+          const double Ssum = g[2 * DP];
+#pragma unroll
+          for (int k = 0; k < DP; ++k) {
+            const double x = a.xhat[i * DP + k];
+            acc[k] = x * x * Ssum - 2.0 * x * (double)g[k] + (double)g[DP + k];
+          }
+          acc[DP] = Ssum;
+        }
+      } else if (sp == 0 && i < a.n) {
+        // diagonal W_ii for the lambda component, once per row
+        float wii = 0.f;
+        for (int m = 0; m < a.M; ++m)
+          wii = fmaf(a.sa[m] * a.A[(long long)a.amap[m] * a.ld + i],
+                     a.B[(long long)a.bmap[m] * a.ld + i], wii);
+        acc[DP + 1] = wii;
+      }
+    }
+  }
+
+  // -------- all roles: release tensor memory; CTA reduction; last CTA sums the partials -------
+  if (warp == 1) {
+    if (lane == 0) (void)mbar_wait_spin(done, 0);
+    __syncwarp();
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  if (warp == 1) tc::tmem_dealloc(tbase, kGtCols);
+  if (*s_fail) {
+    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    return;
+  }
+  if (warp >= 2) {
+#pragma unroll
+    for (int k = 0; k < NACC; ++k) {
+      const double v = warp_sum(acc[k]);
+      if (lane == 0) s_red[warp - 2][k] = v;
+    }
+  }
+  __syncthreads();
+  double* part = a.partials + (long long)blockIdx.x * kMaxP;
+  if (tid < NACC) {
+    double v = 0.0;
+    for (int ww = 0; ww < 8; ++ww) v += s_red[ww][tid];
+    // slots: lengthscales 0..d-1, then sigma^2 at d, lambda at d+1
+    if (tid < a.d) part[tid] = v;
+    else if (tid == DP) part[a.d] = v;
+    else if (tid == DP + 1) part[a.d + 1] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) *s_last = (atomicAdd(a.counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!*s_last) return;
+  __threadfence();
+  if (tid < a.d + 2) {
+    double v = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(a.partials + (long long)b * kMaxP + tid);
+    if (tid == a.d + 1) v *= a.params->lambda;
+    a.g_out[tid] = v;
+  }
+  if (tid == 0) *a.counter = 0;
+}
+
+template <int DP, int KS>
+struct GtInst {
+  using S = GtShape<DP, KS>;
+  static int occupancy() {
+    static int occ = -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+      auto fn = grad_tc_kernel<DP, KS>;
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
+      cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      int dev = 0, smem_sm = 0;
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess)
+        smem_sm = 228 * 1024;
+      const int by_smem = smem_sm / (int)(S::SMEM + 2048);
+      occ = std::max(1, std::min({by_smem, (int)(512 / kGtCols), DP >= 16 ? 2 : 3}));
+    });
+    return occ;
+  }
+  static cudaError_t launch(GradLaunch& L, cudaStream_t s) {
+    KmvPlan p = plan_split(L.n, kGtBM, 1, 4, L.num_sms * occupancy());
+    const size_t need = (size_t)p.n_rb * p.nsplit * kMaxP;
+    if (L.plan_only) {
+      L.need_partials_len = need;
+      return cudaSuccess;
+    }
+    if (need > L.partials_len) {
+      L.need_partials_len = need;
+      return cudaErrorMemoryAllocation;
+    }
+    const long long ntiles = (L.n + kGtBN - 1) / kGtBN;
+    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.tc_hi);
+    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.tc_lo);
+    const long long zoff = (long long)kGtZOff * L.tc_ld;
+    {
+      const long long total = ntiles * kGtBN * S::K1;
+      const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * L.num_sms);
+      pack_bt_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.B), L.ld, L.bmap, L.M,
+                                            S::K1, L.n, ntiles, hi, lo);
+    }
+    {
+      const long long total = ntiles * S::N2 * kGtBN;
+      const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * L.num_sms);
+      pack_z_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.xhat), DP, L.n, S::N2,
+                                           ntiles, hi + zoff, lo + zoff);
+    }
+    GtDevArgs a;
+    a.xhat = static_cast<const float*>(L.xhat);
+    a.bneg = L.bneg;
+    a.Bt_hi = hi;
+    a.Bt_lo = lo;
+    a.Zt_hi = hi + zoff;
+    a.Zt_lo = lo + zoff;
+    a.A = static_cast<const float*>(L.A);
+    a.amap = L.amap;
+    a.sa = static_cast<const float*>(L.sa);
+    a.B = static_cast<const float*>(L.B);
+    a.bmap = L.bmap;
+    a.ld = L.ld;
+    a.M = L.M;
+    a.n = L.n;
+    a.d = L.d;
+    a.params = L.params;
+    a.nsplit = p.nsplit;
+    a.tiles_per_split = (int)((ntiles + p.nsplit - 1) / p.nsplit);
+    a.nsplit = (int)((ntiles + a.tiles_per_split - 1) / a.tiles_per_split);
+    a.ntiles = (int)ntiles;
+    a.partials = L.partials;
+    a.counter = L.counter;
+    a.g_out = L.g_out;
+    a.status = L.status;
+    const int nrb = (int)((L.n + kGtBM - 1) / kGtBM);
+    grad_tc_kernel<DP, KS><<<nrb * a.nsplit, kGtThreads, S::SMEM, s>>>(a);
+    return cudaGetLastError();
+  }
+};
+
+template <int DP>
+static cudaError_t grad_tc_dispatch_m(GradLaunch& L, cudaStream_t s) {
+  if (L.M <= 16) return GtInst<DP, 1>::launch(L, s);
+  if (L.M <= 32) return GtInst<DP, 2>::launch(L, s);
+  if (L.M <= 64) return GtInst<DP, 4>::launch(L, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s) {
+  if (L.M < 1 || L.M > kMaxM || !L.tc_hi || !L.tc_lo || !L.bneg) return cudaErrorInvalidValue;
+  switch (L.DP) {
+    case 2: return grad_tc_dispatch_m<2>(L, s);
+    case 4: return grad_tc_dispatch_m<4>(L, s);
+    case 8: return grad_tc_dispatch_m<8>(L, s);
+    case 16: return grad_tc_dispatch_m<16>(L, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ulisse

@@ -241,6 +241,12 @@ struct GradLaunch {
   int num_sms;
   size_t need_partials_len;  // set when partials_len is too small
   bool plan_only;            // only fill need_partials_len (no launch)
+  // tensor-core pass (launch_grad_tc) only: row norms (launch_prescale_tc) and BF16 packed
+  // scratch, high and low parts, 112 x tc_ld elements each (tc_ld = n rounded up to 128)
+  const float* bneg;
+  void* tc_hi;
+  void* tc_lo;
+  long long tc_ld;
 };
 
 // Mixed-precision (tcgen05) K V launch: operands prepared by launch_prescale_tc.
@@ -283,6 +289,7 @@ cudaError_t launch_kmv_f64(KmvLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f32(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f64(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_tc(TcLaunch& L, cudaStream_t s);
+cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_prescale_tc(const float* xhat, int DP, int d, long long n, long long ld,
                                float* bneg, int num_sms, cudaStream_t s);
 

@@ -34,7 +34,7 @@ EXPORTED = [
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
-    "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain",
+    "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
 ]
 
 
@@ -115,6 +115,7 @@ def load():
     lib.ulisse_kmv_f64.argtypes = [P, P, I, P, I, P]
     lib.ulisse_solve.argtypes = [P, P, P, I, P, P, P, U64, sp]
     lib.ulisse_grad.argtypes = [P, P, U64, P, sp]
+    lib.ulisse_dk_bilinear.argtypes = [P, P, P, P, I, P, P]
     lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
     lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
     lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
@@ -269,6 +270,24 @@ class Context:
         self._check(st, allow)
         return g, [(s.l, s.iterations, s.outcome, s.J0, s.J1) for s in stats]
 
+    def dk_bilinear(self, psi, A, B, scale=None):
+        """out_i = sum_m scale_m a_m^T dK/dpsi_i b_m for every parameter (host numpy, p).
+        A, B: (n, M) CUDA tensors."""
+        Ac = _colmajor(A.float())
+        Bc = _colmajor(B.float())
+        if Ac.shape != Bc.shape or Ac.shape[0] != self.n:
+            raise ValueError("A and B must both be (n, M)")
+        M = Ac.shape[1]
+        sc = np.ascontiguousarray(scale, dtype=np.float64) if scale is not None else None
+        if sc is not None and sc.shape != (M,):
+            raise ValueError("scale must have M entries")
+        psi = _f64_host(psi, self.p)
+        out = np.zeros(self.p)
+        self._check(self._lib.ulisse_dk_bilinear(self._h, _hptr(psi), ctypes.c_void_p(Ac.data_ptr()),
+                                                 ctypes.c_void_p(Bc.data_ptr()), M, _hptr(sc),
+                                                 _hptr(out)))
+        return out
+
     def sgld_step(self, psi, eps_t, step, M=None, prior_grad=None, allow=()):
         """One SGLD step; returns (psi_new, g) as numpy arrays."""
         psi = np.array(psi, dtype=np.float64, copy=True)
@@ -389,6 +408,10 @@ def ulisse_solve(ctx: Context, psi, B, n_est=None, S0=None, step=0):
 
 def ulisse_grad(ctx: Context, psi, step=0):
     return ctx.grad(psi, step)
+
+
+def ulisse_dk_bilinear(ctx: Context, psi, A, B, scale=None):
+    return ctx.dk_bilinear(psi, A, B, scale)
 
 
 def ulisse_sgld_step(ctx: Context, psi, eps_t, step, M=None, prior_grad=None):

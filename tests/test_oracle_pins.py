@@ -15,6 +15,8 @@ a wrong sign or index, a transposed operand, a wrong weight) fails at least one 
   kmv / dkmv_all /      dense matrix product with numpy on tiny and ragged sizes
   kmv_rows
   exact_gradient        central finite differences of the log marginal likelihood
+  dk_bilinear           unit-vector factors give the hand-written entries of dK/dpsi_i; exact
+                        solves and identity columns as factors give the exact gradient
   log_marginal_lik.     scipy.stats.multivariate_normal.logpdf
   cg_record             Cholesky solution (Sec. 3 error definition), conjugacy and residual
                         orthogonality, n=1 in one step, K ~ c I in one step
@@ -222,6 +224,54 @@ def test_exact_gradient_vs_fd_of_log_marginal_likelihood(orc):
         pm[i] -= h
         fd[i] = (orc.log_marginal_likelihood(X, y, pp) - orc.log_marginal_likelihood(X, y, pm)) / (2 * h)
     assert np.max(np.abs(g - fd)) < 1e-6 * max(1.0, np.max(np.abs(g)))
+
+
+def test_dk_bilinear_unit_vectors(orc):
+    """a = e_p, b = e_q: the (p, q) entry of every derivative matrix, written out by hand:
+    sigma^2 exp(-1/2 sum_k r_k^2) r_k^2 (r_k = (x_pk - x_qk) / l_k) for log l_k, the signal
+    covariance for log sigma^2, lambda [p == q] for log lambda."""
+    X = _rand_X(9, 3, 21)
+    l = np.array([0.4, 0.7, 1.3])
+    sig2, lam = 1.7, 0.2
+    psi = np.log(np.concatenate([l, [sig2, lam]]))
+    for p_, q_ in [(0, 0), (1, 5), (5, 1), (8, 2), (3, 3)]:
+        A = np.zeros((9, 1))
+        B = np.zeros((9, 1))
+        A[p_, 0] = 1.0
+        B[q_, 0] = 1.0
+        out = orc.dk_bilinear(X, psi, A, B, scale=[1.0])
+        r = (X[p_] - X[q_]) / l
+        ks = sig2 * math.exp(-0.5 * float(np.sum(r * r)))
+        want = np.concatenate([ks * r * r, [ks, lam if p_ == q_ else 0.0]])
+        assert np.allclose(out, want, rtol=1e-13, atol=1e-15)
+    # scale and the sum over m: two unit pairs with weights
+    A = np.zeros((9, 2))
+    B = np.zeros((9, 2))
+    A[1, 0] = B[5, 0] = 1.0
+    A[2, 1] = B[2, 1] = 1.0
+    out = orc.dk_bilinear(X, psi, A, B, scale=[2.0, -0.5])
+    one = orc.dk_bilinear(X, psi, A[:, :1], B[:, :1])
+    two = orc.dk_bilinear(X, psi, A[:, 1:], B[:, 1:])
+    assert np.allclose(out, 2.0 * one - 0.5 * two, rtol=1e-13, atol=1e-15)
+
+
+def test_dk_bilinear_gives_the_exact_gradient(orc):
+    """With a_0 = b_0 = K^{-1} y (weight 1/2) and a_k = K^{-1} e_k, b_k = e_k (weight -1/2) the
+    forms are 1/2 y^T K^-1 dK K^-1 y - 1/2 tr(K^-1 dK): the exact gradient, itself pinned by
+    finite differences of the log marginal likelihood."""
+    n = 40
+    X = _rand_X(n, 2, 22)
+    psi = np.log([0.3, 0.5, 1.1, 0.2])
+    y = np.random.default_rng(22).standard_normal(n)
+    K = orc.cov_matrix(X, psi)
+    Kinv = np.linalg.inv(K)
+    alpha = Kinv @ y
+    A = np.column_stack([alpha, Kinv])
+    B = np.column_stack([alpha, np.eye(n)])
+    scale = np.concatenate([[0.5], np.full(n, -0.5)])
+    out = orc.dk_bilinear(X, psi, A, B, scale)
+    g = orc.exact_gradient(X, y, psi)
+    assert np.allclose(out, g, rtol=1e-9, atol=1e-10 * np.max(np.abs(g)))
 
 
 # ----------------------------------------------------------------------------------------
