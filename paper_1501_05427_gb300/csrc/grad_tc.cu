@@ -425,6 +425,24 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   if (tid == 0) *a.counter = 0;
 }
 
+// Split of the j range: every SM works through its share of the (row block, split) items in
+// turn, so the pass takes about ceil(items / SMs) x (tiles per item + a fixed cost per item:
+// the A^ image, the pipeline fill and the reduction, about six tiles' worth).
+static int plan_gt_split(long long n_rb, long long ntiles, int num_sms) {
+  long long best = -1;
+  int best_s = 1;
+  for (int s = 1; s <= 64 && s <= ntiles; ++s) {
+    const long long items = n_rb * s;
+    const long long per = (ntiles + s - 1) / s;
+    const long long cost = (items + num_sms - 1) / num_sms * (per + 6);
+    if (best < 0 || cost < best) {
+      best = cost;
+      best_s = s;
+    }
+  }
+  return best_s;
+}
+
 template <int DP, int KS>
 struct GtInst {
   using S = GtShape<DP, KS>;
@@ -446,8 +464,13 @@ struct GtInst {
     return occ;
   }
   static cudaError_t launch(GradLaunch& L, cudaStream_t s) {
-    KmvPlan p = plan_split(L.n, kGtBM, 1, 4, L.num_sms * occupancy());
-    const size_t need = (size_t)p.n_rb * p.nsplit * kMaxP;
+    (void)occupancy();
+    const long long ntiles = (L.n + kGtBN - 1) / kGtBN;
+    const int n_rb = (int)((L.n + kGtBM - 1) / kGtBM);
+    const int s_plan = plan_gt_split(n_rb, ntiles, L.num_sms);
+    const int tiles_per_split = (int)((ntiles + s_plan - 1) / s_plan);
+    const int nsplit = (int)((ntiles + tiles_per_split - 1) / tiles_per_split);
+    const size_t need = (size_t)n_rb * nsplit * kMaxP;
     if (L.plan_only) {
       L.need_partials_len = need;
       return cudaSuccess;
@@ -456,7 +479,6 @@ struct GtInst {
       L.need_partials_len = need;
       return cudaErrorMemoryAllocation;
     }
-    const long long ntiles = (L.n + kGtBN - 1) / kGtBN;
     __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(L.tc_hi);
     __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(L.tc_lo);
     const long long zoff = (long long)kGtZOff * L.tc_ld;
@@ -489,16 +511,14 @@ struct GtInst {
     a.n = L.n;
     a.d = L.d;
     a.params = L.params;
-    a.nsplit = p.nsplit;
-    a.tiles_per_split = (int)((ntiles + p.nsplit - 1) / p.nsplit);
-    a.nsplit = (int)((ntiles + a.tiles_per_split - 1) / a.tiles_per_split);
+    a.nsplit = nsplit;
+    a.tiles_per_split = tiles_per_split;
     a.ntiles = (int)ntiles;
     a.partials = L.partials;
     a.counter = L.counter;
     a.g_out = L.g_out;
     a.status = L.status;
-    const int nrb = (int)((L.n + kGtBM - 1) / kGtBM);
-    grad_tc_kernel<DP, KS><<<nrb * a.nsplit, kGtThreads, S::SMEM, s>>>(a);
+    grad_tc_kernel<DP, KS><<<n_rb * nsplit, kGtThreads, S::SMEM, s>>>(a);
     return cudaGetLastError();
   }
 };
