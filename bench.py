@@ -52,13 +52,33 @@ KMV_KERNELS = {
               "paper_1501_05427_gb300/csrc/kmv_launch.cuh",
               "paper_1501_05427_gb300/csrc/kmv_f32.cu",
               "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
-    "mixed": ("kmv_tc_kernel (tile-generating K V, tcgen05 BF16x3, FP32 accumulation)",
-              os.path.join(ROOT, "profiles", "kmv_tc_census_like_traffic.txt"),
-              ["paper_1501_05427_gb300/csrc/kmv_tc.cu",
-               "paper_1501_05427_gb300/csrc/tc_common.cuh",
-               "paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
-               "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
+    "mixed_pipe": ("kmv_tc_kernel (tile-generating K V, tcgen05 BF16x3 contraction, "
+                   "FP32-FMA cross term)",
+                   os.path.join(ROOT, "profiles", "kmv_tc_census_like_traffic.txt"),
+                   ["paper_1501_05427_gb300/csrc/kmv_tc.cu",
+                    "paper_1501_05427_gb300/csrc/tc_common.cuh",
+                    "paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
+                    "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
+    "mixed_tensor": ("kmv_tc2_kernel (tile-generating K V, tcgen05 3xTF32 cross term and "
+                     "BF16x3 contraction, FP32 accumulation)",
+                     os.path.join(ROOT, "profiles", "kmv_tc2_census_like_traffic.txt"),
+                     ["paper_1501_05427_gb300/csrc/kmv_tc2.cu",
+                      "paper_1501_05427_gb300/csrc/kmv_tc.cu",
+                      "paper_1501_05427_gb300/csrc/tc_common.cuh",
+                      "paper_1501_05427_gb300/csrc/kmv_kernel.cuh",
+                      "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
 }
+CROSS_KEY = {1: "mixed_pipe", 2: "mixed_tensor"}
+
+
+def kernel_key(path, tune_table=None, live_cols=None):
+    """KMV_KERNELS key of the K V kernel a path runs at live_cols columns: the tensor-core path
+    forms the cross term where the autotuner chose (default: on the tensor cores)."""
+    if path == "fp32":
+        return "fp32"
+    if tune_table and live_cols and tune_table[live_cols - 1].get("cross_term"):
+        return CROSS_KEY[tune_table[live_cols - 1]["cross_term"]]
+    return "mixed_tensor"
 
 
 def parse_args():
@@ -102,9 +122,9 @@ def _kv_file(path):
     return out
 
 
-def kmv_source_hash(path="fp32"):
+def kmv_source_hash(key="fp32"):
     h = hashlib.sha256()
-    for f in KMV_KERNELS[path][2]:
+    for f in KMV_KERNELS[key][2]:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -439,7 +459,8 @@ def run_ours(args):
                 "step_time_fit": _fit_step_time(ores["step_ms"], ores["rounds"]),
                 "kv_entry_rhs_per_s": oprof["kv_entry_rhs_per_s"],
                 "kmv_ms_per_round": (oprof["kmv_ms"] / oprof["rounds"] if oprof["rounds"] else None),
-                "kernel": KMV_KERNELS[path][0], "probe_refresh": refresh,
+                "kernel": KMV_KERNELS[kernel_key(path, tuned.get(key), R)][0],
+                "probe_refresh": refresh,
                 "warm_started_solves": bool(warm_leg)}
 
     plain = same_method = None
@@ -459,10 +480,11 @@ def run_ours(args):
         at_equal = {"rounds_per_step": r_bar, "chosen_steps_per_s": 1000.0 / t_c,
                     "fp32_steps_per_s": 1000.0 / t_p, "speedup": t_p / t_c,
                     "fp32_leg": "fp32_same_method" if same_method else "plain_fp32"}
-    name, traffic_file, _ = KMV_KERNELS[args.path]
+    kkey = kernel_key(args.path, tuned.get("chosen"), R)
+    name, traffic_file, _ = KMV_KERNELS[kkey]
     traffic = None
     tf = _kv_file(traffic_file)
-    if tf and tf.get("kmv_source_hash") == kmv_source_hash(args.path):
+    if tf and tf.get("kmv_source_hash") == kmv_source_hash(kkey):
         traffic = float(tf["dram_bytes_per_launch"])
     kmv_tflops = prof["kmv_tflops"]
     roofline = {
@@ -503,7 +525,8 @@ def run_ours(args):
         "plain_fp32": plain,
         "fp32_same_method": same_method,
         "autotune": ({path: {"tuned_over_untuned_ms": [round(e["ms"] / e["ms_default"], 3)
-                                                      for e in tab]}
+                                                      for e in tab],
+                             "cross_term": [e["cross_term"] for e in tab]}
                       for path, tab in tuned.items()} if tuned else None),
         "gradient_error": ({k: grad_err[k] for k in grad_err} if grad_err else None),
         "mvp_rounds_per_step": rounds / K,

@@ -83,6 +83,12 @@ typedef struct {
     int kmv_rows_per_thread; /* K V tile shape: output rows per thread, 2 or 4; 0 = the
                                 tuned default.  Changes the summation order of the split
                                 j range, hence the last bits of the results. */
+    int tc_cross_term;       /* mixed precision: where the cross term x^_i . x^_j of the
+                                kernel values is formed -- 1 = FP32 FMAs on the CUDA cores,
+                                2 = three TF32 products on the tensor cores (x^ split into a
+                                TF32 high part and the remainder), 0 = the default (2) or the
+                                autotuner's choice.  The two differ in the last bits of each
+                                kernel value (relative 1e-6 to 1e-5). */
 } ulisse_config;
 
 /* Fill *cfg with the paper's settings: FP32, 4 Rademacher probes redrawn every step,
@@ -421,10 +427,14 @@ typedef struct {
     int nsplit;              /* j-range split count forced (0: the launch plan's choice) */
     float ms;                /* median time of the chosen configuration */
     float ms_default;        /* median time of the untuned configuration */
+    int cross_term;          /* tensor-core path: where the cross term is formed (1 FP32
+                                FMAs, 2 tensor cores; see ulisse_config.tc_cross_term);
+                                0 on the SIMT path */
 } ulisse_tune_entry;
 
 /* Time, for every live column count 1..max_cols (<= 32), the candidate K V configurations
- * on this context's data -- compiled column counts, rows per thread, j-range splits -- with
+ * on this context's data -- compiled column counts, rows per thread (SIMT), where the cross
+ * term is formed (tensor-core path), j-range splits -- with
  * CUDA events on the context's stream (median of `reps` launches each), and use the
  * fastest from then on (the untuned choice is always a candidate).  psi: host, the
  * parameters to tune at (they set the data layout only; any valid psi).  out: NULL or

@@ -28,6 +28,7 @@ struct ulisse_ctx {
   float* bneg = nullptr;      // -log2(e)/2 |x^|^2 per input (tensor-core path)
   void *Vt_hi = nullptr, *Vt_lo = nullptr;
   void *Gt_hi = nullptr, *Gt_lo = nullptr;   // packed operands of the tensor-core gradient
+  float *Xt_hi = nullptr, *Xt_lo = nullptr;  // TF32 images A | B (tensor-core cross term)
 
   float* X = nullptr;         // raw inputs, n x d row-major
   void* y = nullptr;          // labels, ldn (element type T)
@@ -89,7 +90,7 @@ struct ulisse_ctx {
 
   // autotuned K V launch configuration per live column count (ulisse_autotune); index
   // nl - 1, empty until tuned
-  struct KmvTune { int width, tm, nsplit; float ms, ms_default; };
+  struct KmvTune { int width, tm, nsplit; float ms, ms_default; int cross; };
   std::vector<KmvTune> tune;
   int last_nsplit = 1;        // split count of the last K V launch (or plan)
 
@@ -300,7 +301,10 @@ static ulisse_status prescale(ulisse_ctx* ctx) {
   if (ctx->mixed) {
     CK(launch_prescale_tc((const float*)ctx->xhat, ctx->DP, ctx->d, ctx->n, ctx->ld128,
                           ctx->bneg, ctx->num_sms, ctx->stream));
-    if (!ctx->capturing) ctx->launches++;
+    CK(launch_pack_x_tf32((const float*)ctx->xhat, ctx->bneg, ctx->params, ctx->DP, ctx->n,
+                          ctx->ld128, ctx->Xt_hi, ctx->Xt_lo, ctx->ld128 * 24, ctx->num_sms,
+                          ctx->stream));
+    if (!ctx->capturing) ctx->launches += 2;
   }
   return ULISSE_OK;
 }
@@ -347,13 +351,23 @@ static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap,
     L.params = ctx->params;
     L.status = ctx->status_dev;
     L.num_sms = ctx->num_sms;
+    L.X_hi = ctx->Xt_hi;
+    L.X_lo = ctx->Xt_lo;
+    L.X_off = ctx->ld128 * 24;
+    // where the cross term is formed: the tuned choice, else the configured one (default:
+    // tensor cores)
+    int cross = ctx->cfg.tc_cross_term != 0 ? ctx->cfg.tc_cross_term : kCrossTensor;
     if ((int)ctx->tune.size() >= L.R && ctx->tune[L.R - 1].width > 0) {
       L.n_min = ctx->tune[L.R - 1].width;
       L.nsplit = ctx->tune[L.R - 1].nsplit;
+      if (ctx->tune[L.R - 1].cross != 0) cross = ctx->tune[L.R - 1].cross;
     }
+    auto launch = [&](TcLaunch& LL) {
+      return cross == kCrossTensor ? launch_kmv_tc2(LL, ctx->stream) : launch_kmv_tc(LL, ctx->stream);
+    };
     if (ctx->planning) {
       L.plan_only = true;
-      cudaError_t e = launch_kmv_tc(L, ctx->stream);
+      cudaError_t e = launch(L);
       ctx->last_nsplit = L.planned_nsplit;
       if (e != cudaSuccess)
         return fail(ctx, ULISSE_ERR_CUDA, std::string("tensor-core K V plan: ") + cudaGetErrorString(e));
@@ -367,7 +381,7 @@ static ulisse_status run_kmv_tc(ulisse_ctx* ctx, const void* V, const int* vmap,
       L.counters_len = ctx->counters_len;
       cudaEvent_t ea = nullptr, eb = nullptr;
       prof_begin(ctx, &ea, &eb);
-      cudaError_t e = launch_kmv_tc(L, ctx->stream);
+      cudaError_t e = launch(L);
       if (ctx->prof) {
         if (e == cudaSuccess)
           prof_end(ctx, 0, ea, eb, (double)ctx->n * ctx->n * (3.0 * ctx->d + 2.0 + 2.0 * L.R));
@@ -757,6 +771,7 @@ static ulisse_status check_cfg(const ulisse_config* c) {
     return ULISSE_ERR_ARG;
   if (c->kmv_rows_per_thread != 0 && c->kmv_rows_per_thread != 2 && c->kmv_rows_per_thread != 4)
     return ULISSE_ERR_ARG;
+  if (c->tc_cross_term < 0 || c->tc_cross_term > 2) return ULISSE_ERR_ARG;
   return ULISSE_OK;
 }
 
@@ -813,7 +828,9 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
         (s = dev_alloc(ctx, &ctx->Vt_hi, 2 * ctx->ld128 * 64)) ||
         (s = dev_alloc(ctx, &ctx->Vt_lo, 2 * ctx->ld128 * 64)) ||
         (s = dev_alloc(ctx, &ctx->Gt_hi, 2 * ctx->ld128 * 112)) ||
-        (s = dev_alloc(ctx, &ctx->Gt_lo, 2 * ctx->ld128 * 112)))
+        (s = dev_alloc(ctx, &ctx->Gt_lo, 2 * ctx->ld128 * 112)) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->Xt_hi), 4 * ctx->ld128 * 48)) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->Xt_lo), 4 * ctx->ld128 * 48)))
       return bail(s);
   }
   if (cudaMallocHost(&ctx->h_n_live, sizeof(int)) != cudaSuccess ||
@@ -876,6 +893,7 @@ void ulisse_config_default(ulisse_config* cfg) {
   cfg->max_iter = 1000;
   cfg->seed = 0;
   cfg->kmv_rows_per_thread = 0;
+  cfg->tc_cross_term = 0;
 }
 
 ulisse_status ulisse_create(ulisse_ctx** out, const float* X, const float* y, long long n, int d,
@@ -1347,7 +1365,7 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
   // what one launch does outside the CG loop (the loop's share is counted on the device)
   const long long kmv_per = ctx->mixed ? 2 : 1, kmv_cols = ctx->mixed ? 64 : kMaxRChunk;
   const int init_cols = warm ? R : s0_cols;   // columns of the product K s_0
-  ctx->graph_launches_fixed = (ctx->mixed ? 2 : 1) + 1 + 1 + (ctx->mixed ? 3 : 1) + 1 +
+  ctx->graph_launches_fixed = (ctx->mixed ? 3 : 1) + 1 + 1 + (ctx->mixed ? 3 : 1) + 1 +
       (s0_cols > 0 ? 2 : 0) +
       (init_cols > 0 ? kmv_per * ((init_cols + kmv_cols - 1) / kmv_cols) : 0);
   ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + init_cols);
@@ -2339,10 +2357,11 @@ ulisse_status ulisse_batch_sgld_chain(ulisse_ctx* ctx, double* psi_dev, const do
 // Median time of `reps` K V launches over nl columns in the given configuration (width 0:
 // the default choices); *nsplit_out gets the split count the configuration used.
 static ulisse_status time_kmv_config(ulisse_ctx* ctx, int nl, int width, int tm, int nsplit,
-                                     int reps, float* ms_out, int* nsplit_out) {
-  if ((int)ctx->tune.size() < nl) ctx->tune.resize((size_t)nl, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f});
+                                     int cross, int reps, float* ms_out, int* nsplit_out) {
+  if ((int)ctx->tune.size() < nl)
+    ctx->tune.resize((size_t)nl, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f, 0});
   const ulisse_ctx::KmvTune saved = ctx->tune[nl - 1];
-  ctx->tune[nl - 1] = ulisse_ctx::KmvTune{width, tm, nsplit, 0.f, 0.f};
+  ctx->tune[nl - 1] = ulisse_ctx::KmvTune{width, tm, nsplit, 0.f, 0.f, cross};
   ctx->planning = true;
   ulisse_status r = run_kmv(ctx, ctx->D, ctx->iota, nl, ctx->KD, ctx->iota, kModeK, -1);
   ctx->planning = false;
@@ -2387,34 +2406,43 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
   CKS(ensure_columns(ctx, max_cols, max_cols));
   const bool prof = ctx->prof;
   ctx->prof = false;
-  ctx->tune.assign((size_t)max_cols, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f});
+  ctx->tune.assign((size_t)max_cols, ulisse_ctx::KmvTune{0, 0, 0, 0.f, 0.f, 0});
   std::vector<ulisse_ctx::KmvTune> table((size_t)max_cols);
   ulisse_status r = ULISSE_OK;
   for (int nl = 1; nl <= max_cols && r == ULISSE_OK; ++nl) {
     // the default configuration first (what the launch plan picks untuned)
     float ms_def = 0.f;
     int split_def = 1;
-    r = time_kmv_config(ctx, nl, 0, 0, 0, reps, &ms_def, &split_def);
+    r = time_kmv_config(ctx, nl, 0, 0, 0, 0, reps, &ms_def, &split_def);
     if (r != ULISSE_OK) break;
-    ulisse_ctx::KmvTune best{0, 0, 0, ms_def, ms_def};
+    const int cross_def =
+        ctx->mixed ? (ctx->cfg.tc_cross_term != 0 ? ctx->cfg.tc_cross_term : kCrossTensor) : 0;
+    ulisse_ctx::KmvTune best{0, 0, 0, ms_def, ms_def, cross_def};
     // candidates: the compiled width (tensor cores: the MMA N; SIMT: the smallest
-    // instantiation >= nl, or a larger one), rows per thread (SIMT), then the j split
-    std::vector<int> widths, tms;
+    // instantiation >= nl, or a larger one), rows per thread (SIMT) or where the cross term
+    // is formed (tensor cores, unless the configuration fixes it), then the j split
+    std::vector<int> widths, tms, crosses;
     if (ctx->mixed) {
       for (int wd : {16, 32, 64})
         if (wd >= nl) widths.push_back(wd);
       tms = {0};
+      if (ctx->cfg.tc_cross_term != 0) crosses = {ctx->cfg.tc_cross_term};
+      else crosses = {kCrossPipe, kCrossTensor};
     } else {
       widths = {nl, nl + 1, nl + 4};
       tms = {2, 4};
+      crosses = {0};
     }
     for (int wd : widths) {
       for (int tm : tms) {
-        float ms = 0.f;
-        int sp = 1;
-        r = time_kmv_config(ctx, nl, wd, tm, 0, reps, &ms, &sp);
+        for (int cr : crosses) {
+          float ms = 0.f;
+          int sp = 1;
+          r = time_kmv_config(ctx, nl, wd, tm, 0, cr, reps, &ms, &sp);
+          if (r != ULISSE_OK) break;
+          if (ms < best.ms) best = ulisse_ctx::KmvTune{wd, tm, 0, ms, ms_def, cr};
+        }
         if (r != ULISSE_OK) break;
-        if (ms < best.ms) best = ulisse_ctx::KmvTune{wd, tm, 0, ms, ms_def};
       }
       if (r != ULISSE_OK) break;
     }
@@ -2422,13 +2450,14 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
     const int wd = best.width > 0 ? best.width : nl;
     float ms_base = 0.f;
     int base = 1;
-    r = time_kmv_config(ctx, nl, wd, best.tm, 0, 1, &ms_base, &base);   // its planned split
+    r = time_kmv_config(ctx, nl, wd, best.tm, 0, best.cross, 1, &ms_base, &base);   // its planned split
     for (int sp : {base / 2, base * 2}) {
       if (r != ULISSE_OK || sp < 1 || sp == base) continue;
       float ms = 0.f;
       int used = sp;
-      r = time_kmv_config(ctx, nl, wd, best.tm, sp, reps, &ms, &used);
-      if (r == ULISSE_OK && ms < best.ms) best = ulisse_ctx::KmvTune{wd, best.tm, sp, ms, ms_def};
+      r = time_kmv_config(ctx, nl, wd, best.tm, sp, best.cross, reps, &ms, &used);
+      if (r == ULISSE_OK && ms < best.ms)
+        best = ulisse_ctx::KmvTune{wd, best.tm, sp, ms, ms_def, best.cross};
     }
     if (r != ULISSE_OK) break;
     if (best.width == 0) best.width = nl;
@@ -2445,7 +2474,7 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
   if (out)
     for (int nl = 1; nl <= max_cols; ++nl) {
       const ulisse_ctx::KmvTune& t = table[nl - 1];
-      out[nl - 1] = ulisse_tune_entry{nl, t.width, t.tm, t.nsplit, t.ms, t.ms_default};
+      out[nl - 1] = ulisse_tune_entry{nl, t.width, t.tm, t.nsplit, t.ms, t.ms_default, t.cross};
     }
   CK(cudaStreamSynchronize(ctx->stream));
   return ULISSE_OK;
@@ -2489,6 +2518,7 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   for (void** p : {reinterpret_cast<void**>(&ctx->st_next), reinterpret_cast<void**>(&ctx->part1),
                    reinterpret_cast<void**>(&ctx->part2), reinterpret_cast<void**>(&ctx->bneg),
                    &ctx->Vt_hi, &ctx->Vt_lo, &ctx->Gt_hi, &ctx->Gt_lo,
+                   reinterpret_cast<void**>(&ctx->Xt_hi), reinterpret_cast<void**>(&ctx->Xt_lo),
                    reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa})
     dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,

@@ -350,6 +350,15 @@ __global__ void __launch_bounds__(kTcThreads, 3) kmv_tc_kernel(const TcDevArgs a
   if (tid == 0) a.counters[rb] = 0;
 }
 
+// The BF16 high/low images of the operand columns for an N-column MMA (every K V launch).
+void launch_pack_v(const TcLaunch& L, int N, long long ntiles, cudaStream_t s) {
+  const long long total = ntiles * N * kTcBN;
+  const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * L.num_sms);
+  pack_v_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.V), L.ldv, L.vmap, L.R, N,
+                                       L.n, ntiles, static_cast<__nv_bfloat16*>(L.V_hi),
+                                       static_cast<__nv_bfloat16*>(L.V_lo));
+}
+
 template <int DP, int N>
 struct TcInst {
   // CTAs per SM: shared memory (the runtime's occupancy query may assume a smaller
@@ -388,13 +397,7 @@ struct TcInst {
       return cudaErrorMemoryAllocation;
     }
     const long long ntiles = (L.n + kTcBN - 1) / kTcBN;
-    {
-      const long long total = ntiles * N * kTcBN;
-      const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * L.num_sms);
-      pack_v_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.V), L.ldv, L.vmap, L.R, N,
-                                           L.n, ntiles, static_cast<__nv_bfloat16*>(L.V_hi),
-                                           static_cast<__nv_bfloat16*>(L.V_lo));
-    }
+    launch_pack_v(L, N, ntiles, s);
     TcDevArgs a;
     a.xhat = L.xhat;
     a.bneg = L.bneg;

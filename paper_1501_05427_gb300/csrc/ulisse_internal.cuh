@@ -152,6 +152,17 @@ __device__ inline bool mbar_wait_spin(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// Bounded wait for a single thread with nothing else to do meanwhile (a producer or an MMA
+// issuer): it sleeps between polls so that polling takes no issue slots from the warps that
+// compute (about a second at most, then false).
+__device__ inline bool mbar_wait_backoff(uint64_t* bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    __nanosleep(64);
+  }
+  return false;
+}
+
 __device__ inline float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -189,6 +200,10 @@ __device__ inline double block_sum(double v, double* scratch /* >= NT/32 */) {
 // Launch descriptors.
 // ------------------------------------------------------------------------------------
 enum KmvMode { kModeK = 0, kModeDLen = 1, kModeDSig = 2 };
+
+// Where the mixed path forms the cross term x^_i . x^_j (ulisse_config.tc_cross_term).
+constexpr int kCrossPipe = 1;     // FP32 FMAs in the epilogue (kmv_tc_kernel)
+constexpr int kCrossTensor = 2;   // 3xTF32 on the tensor cores (kmv_tc2_kernel)
 
 struct KmvLaunch {
   const void* xhat;      // ldn x DP prescaled inputs (x / l), zero padded
@@ -277,6 +292,11 @@ struct TcLaunch {
   size_t need_partials_bytes;
   int need_counters;
   bool plan_only;        // only fill need_* (no launch): sizing scratch ahead of a capture
+  // tensor-core cross term (launch_kmv_tc2): TF32 images of the augmented rows
+  // (launch_pack_x_tf32): A rows at X_hi / X_lo, B rows X_off floats further on
+  const float* X_hi;
+  const float* X_lo;
+  long long X_off;
 };
 
 // Launchers (return cudaSuccess or the launch error).
@@ -290,6 +310,11 @@ cudaError_t launch_grad_f32(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_f64(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_tc(TcLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s);
+cudaError_t launch_kmv_tc2(TcLaunch& L, cudaStream_t s);
+void launch_pack_v(const TcLaunch& L, int N, long long ntiles, cudaStream_t s);
+cudaError_t launch_pack_x_tf32(const float* xhat, const float* bneg, const DevParams* params,
+                               int DP, long long n, long long ld128, float* X_hi, float* X_lo,
+                               long long X_off, int num_sms, cudaStream_t s);
 cudaError_t launch_prescale_tc(const float* xhat, int DP, int d, long long n, long long ld,
                                float* bneg, int num_sms, cudaStream_t s);
 

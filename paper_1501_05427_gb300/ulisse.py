@@ -51,6 +51,7 @@ class ulisse_config(ctypes.Structure):
         ("max_iter", ctypes.c_int),
         ("seed", ctypes.c_ulonglong),
         ("kmv_rows_per_thread", ctypes.c_int),
+        ("tc_cross_term", ctypes.c_int),
     ]
 
 
@@ -81,7 +82,8 @@ class ulisse_ws_state(ctypes.Structure):
 class ulisse_tune_entry(ctypes.Structure):
     _fields_ = [("live_cols", ctypes.c_int), ("width", ctypes.c_int),
                 ("rows_per_thread", ctypes.c_int), ("nsplit", ctypes.c_int),
-                ("ms", ctypes.c_float), ("ms_default", ctypes.c_float)]
+                ("ms", ctypes.c_float), ("ms_default", ctypes.c_float),
+                ("cross_term", ctypes.c_int)]
 
 
 class UlisseError(RuntimeError):
