@@ -7,17 +7,18 @@
 //      sides split into a TF32 high part and the remainder, three products (Ah Bh + Ah Bl +
 //      Al Bh), FP32 accumulation into a 32-column tensor-memory buffer;
 //   2. the epilogue warps read C back (tcgen05.ld) and form
-//          k_ij = exp2(min(a_i + C_ij, log2 sigma^2)),   a_i = log2(sigma^2) - c1 |x^_i|^2
-//      (one FADD, one min, one ex2 per entry), split k into BF16 high and low parts and store
-//      them over C's own columns (tcgen05.st);
+//          k_ij = exp2(a_i + C_ij),   a_i = log2(sigma^2) - c1 |x^_i|^2
+//      (one FADD and one ex2 per entry), split k into BF16 high and low parts and store them
+//      over C's own columns (tcgen05.st);
 //   3. U_I += K_IJ V_J on the tensor cores with V split into BF16 high + low parts (three
 //      products), FP32 accumulation in tensor memory, as in the FP32-pipe variant.
 // The TF32 images of A and B (high and low parts, K-major canonical, 32-point tiles back to
 // back so that four tiles form the 128-row A operand) are written once per parameter value by
 // pack_x_tf32_kernel.  Roles: warp 0 streams the A image once, then the B_J image and V_J
-// into a 4-stage ring with bulk copies; one thread of warp 1 issues the MMAs; eight
-// epilogue warps (a tensor-memory lane quadrant and half of the tile's 32 columns each) make
-// the kernel values.  Three C/K buffers (two when the accumulator takes 64 columns); a buffer
+// into a 3- or 4-stage ring with bulk copies; one thread of warp 1 issues the MMAs; eight
+// epilogue warps make the kernel values, in two sets of four (one per tensor-memory lane
+// quadrant) that take alternate tiles whole, so that each wait and hand-off covers 32
+// entries per thread.  Three C/K buffers (two when the accumulator takes 64 columns); a buffer
 // is refilled only after the MMAs that read it have completed.  Every wait is bounded.  The split j range, the fixed-order fix-up of the
 // partial sums and the FP32 diagonal term lambda V are those of the FP32-pipe variant.
 #include <cuda_bf16.h>
@@ -104,8 +105,10 @@ struct Tc2Shape {
   static constexpr uint32_t OFF_BARS = OFF_STAGES + ST * STAGE_BYTES;
   // C/K buffers of 32 columns: three while they fit beside the accumulator, else two
   static constexpr int NB = (3 * 32 + N <= (int)kT2Cols) ? 3 : 2;
-  // full, empty per stage; a_full; c_full, k_full, b_free per buffer; done
-  static constexpr int NBARS = 2 * ST + 1 + 3 * NB + 1;
+  // full, empty per stage; a_full; c_full per tile mod 6 (so that each barrier serves one
+  // epilogue set and its phases are waited in order); k_full, b_free per buffer; done
+  static constexpr int NCF = 6;
+  static constexpr int NBARS = 2 * ST + 1 + NCF + 2 * NB + 1;
   static constexpr uint32_t SMEM = OFF_BARS + NBARS * 8 + 64;
   static constexpr uint32_t COL_U = NB * 32;   // after the C/K buffers
   static_assert(COL_U + N <= kT2Cols, "tensor memory layout exceeds the allocation");
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
   uint64_t* empty = bars + ST;
   uint64_t* a_full = bars + 2 * ST;
   uint64_t* c_full = a_full + 1;
-  uint64_t* k_full = c_full + NB;
+  uint64_t* k_full = c_full + S::NCF;
   uint64_t* b_free = k_full + NB;
   uint64_t* done = b_free + NB;
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + S::OFF_BARS + S::NBARS * 8);
@@ -172,9 +175,9 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
       mbar_init(&empty[s], 1);   // the MMA commit: only the tensor cores read a stage
     }
     mbar_init(a_full, 1);
+    for (int c = 0; c < S::NCF; ++c) mbar_init(&c_full[c], 1);
     for (int b = 0; b < NB; ++b) {
-      mbar_init(&c_full[b], 1);
-      mbar_init(&k_full[b], 8);
+      mbar_init(&k_full[b], 4);   // the four epilogue warps of the tile's set
       mbar_init(&b_free[b], 1);
     }
     mbar_init(done, 1);
@@ -235,7 +238,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
             tc::mma_tf32(dC, tc::smem_desc(A + ks * 256, 128, sbo_x),
                          tc::smem_desc(B + ks * 256, 128, sbo_x), idesc_c, (term | ks) != 0);
         }
-        tc::commit(&c_full[b]);
+        tc::commit(&c_full[p % S::NCF]);
         return true;
       };
       if (ok) tc::fence_after();
@@ -270,37 +273,42 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
       tc::commit(done);
     }
   } else {
-    // ---------------- epilogue: 8 warps, (lane quadrant, column half) each ----------------
+    // ------ epilogue: 8 warps; warp (lane quadrant eq, set h) takes the tiles h, h + 2, ...
+    //        with all 32 of their columns, in two 16-column halves ------
     const int eq = warp & 3;
-    const int half = (warp - 2) >> 2;
+    const int half = (warp - 2) >> 2;   // tile set; also the half of U it reads back
     const int il = eq * 32 + lane;
     const long long i = row0 + il;
     const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
-    const float c0 = a.params->c0f;
-    const float ai = c0 + a.bneg[i];   // bneg covers the padded rows (zero there)
+    const float ai = a.params->c0f + a.bneg[i];   // bneg covers the padded rows (zero there)
     bool ok = true;
-    for (int lt = 0; lt < nt; ++lt) {
+    for (int lt = half; lt < nt; lt += 2) {
       const int b = lt % NB;
-      const bool ready = t2_warp_wait(&c_full[b], (uint32_t)((lt / NB) & 1));
+      const bool ready = t2_warp_wait(&c_full[lt % S::NCF], (uint32_t)((lt / S::NCF) & 1));
       if (!__all_sync(0xffffffffu, ready && !*s_fail)) { ok = false; break; }
       tc::fence_after();
-      const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32 + half * 16);
-      float c[16];
-      tc::tmem_ld16(ccol, c);
-      uint32_t hi[8], lo[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float k0 = ex2_approx(fminf(ai + c[2 * q], c0));
-        const float k1 = ex2_approx(fminf(ai + c[2 * q + 1], c0));
-        const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
-        hi[q] = *reinterpret_cast<const uint32_t*>(&h);
-        lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+      for (int hh = 0; hh < 2; ++hh) {
+        // columns [16 hh, 16 hh + 16): C read back, K written over them (high parts, then
+        // low parts: the A operand of the contraction's k-step hh)
+        const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32 + hh * 16);
+        float c[16];
+        tc::tmem_ld16(ccol, c);
+        uint32_t hi[8], lo[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          // the exponent is <= log2 sigma^2 up to rounding (about 1e-6 relative in k)
+          const float k0 = ex2_approx(ai + c[2 * q]);
+          const float k1 = ex2_approx(ai + c[2 * q + 1]);
+          const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
+          hi[q] = *reinterpret_cast<const uint32_t*>(&h);
+          lo[q] = *reinterpret_cast<const uint32_t*>(&l);
+        }
+        tc::tmem_st8(ccol, hi);
+        tc::tmem_st8(ccol + 8, lo);
       }
-      // K over this warp's own 16 C columns: high parts first, then low parts
-      tc::tmem_st8(ccol, hi);
-      tc::tmem_st8(ccol + 8, lo);
       tc::tmem_wait_st();
       tc::fence_before();
       __syncwarp();
