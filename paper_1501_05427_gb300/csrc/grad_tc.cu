@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = *s_tmem;
+  int issued = 0;   // tiles whose copies the producer started (lane 0 of warp 0)
 
   double acc[NACC];
 #pragma unroll
@@ -231,6 +232,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
         bulk_g2s(bt + 2 * S::BT_BYTES, a.Zt_hi + t * N2 * kGtBN, S::Z_BYTES, &full[s]);
         bulk_g2s(bt + 2 * S::BT_BYTES + S::Z_BYTES, a.Zt_lo + t * N2 * kGtBN, S::Z_BYTES,
                  &full[s]);
+        issued = lt + 1;
       }
     }
   } else if (warp == 1) {
@@ -390,7 +392,12 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   tc::fence_after();
   if (warp == 1) tc::tmem_dealloc(tbase, kGtCols);
   if (*s_fail) {
-    if (tid == 0) atomicOr(a.status, kStatusTimeout);
+    if (tid == 0) {
+      atomicOr(a.status, kStatusTimeout);
+      // let the copies still in flight land before the CTA's shared memory goes away
+      for (int lt2 = max(0, issued - S::ST); lt2 < issued; ++lt2)
+        (void)mbar_wait_bounded(&full[lt2 % S::ST], (uint32_t)((lt2 / S::ST) & 1));
+    }
     return;
   }
   if (warp >= 2) {
@@ -430,8 +437,10 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
 // the A^ image, the pipeline fill and the reduction, about six tiles' worth).
 static int plan_gt_split(long long n_rb, long long ntiles, int num_sms) {
   long long best = -1;
-  int best_s = 1;
-  for (int s = 1; s <= 64 && s <= ntiles; ++s) {
+  // no more than kTcMaxSplitTiles tiles per CTA: the sums accumulate in FP32 in tensor memory
+  const int s_min = (int)((ntiles + kTcMaxSplitTiles - 1) / kTcMaxSplitTiles);
+  int best_s = s_min;
+  for (int s = s_min; s <= std::max(64, s_min) && s <= ntiles; ++s) {
     const long long items = n_rb * s;
     const long long per = (ntiles + s - 1) / s;
     const long long cost = (items + num_sms - 1) / num_sms * (per + 6);

@@ -294,4 +294,20 @@ inline KmvPlan plan_split_forced(long long n, int BM, int R, int elem, int nspli
   return p;
 }
 
+// Tensor-core K V accumulates a CTA's whole j range in FP32 in tensor memory, so its rounding
+// grows with the range: at most kTcMaxSplitTiles 32-point tiles per CTA (20,480 points).  At
+// n = 50,000 a range of 16,700 points kept the two cross-term forms within 2e-6 of each other
+// (relative to max |U|), the whole range (50,000) gave 1.4e-4.
+constexpr int kTcMaxSplitTiles = 640;
+
+inline KmvPlan tc_bound_split(KmvPlan p, long long n, int BM, int R, int BN) {
+  const long long nt = (n + BN - 1) / BN;
+  const long long tps = (nt + p.nsplit - 1) / p.nsplit;
+  if (tps <= kTcMaxSplitTiles) return p;
+  const int s = (int)((nt + kTcMaxSplitTiles - 1) / kTcMaxSplitTiles);
+  p.nsplit = s;
+  p.partial_bytes = (size_t)p.n_rb * s * R * BM * 4;
+  return p;
+}
+
 }  // namespace ulisse

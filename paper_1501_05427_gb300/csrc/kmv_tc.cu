@@ -384,6 +384,7 @@ struct TcInst {
   static cudaError_t launch(TcLaunch& L, cudaStream_t s) {
     KmvPlan p = L.nsplit > 0 ? plan_split_forced(L.n, kTcBM, N, 4, L.nsplit)
                              : plan_split(L.n, kTcBM, N, 4, L.num_sms * occupancy());
+    p = tc_bound_split(p, L.n, kTcBM, N, kTcBN);
     const size_t pbytes = p.nsplit > 1 ? (size_t)p.n_rb * p.nsplit * N * kTcBM * 4 : 0;
     L.planned_nsplit = p.nsplit;
     if (L.plan_only) {

@@ -407,6 +407,7 @@ struct Tc2Inst {
   static cudaError_t launch(TcLaunch& L, cudaStream_t s) {
     KmvPlan p = L.nsplit > 0 ? plan_split_forced(L.n, kT2BM, N, 4, L.nsplit)
                              : plan_split(L.n, kT2BM, N, 4, L.num_sms * occupancy());
+    p = tc_bound_split(p, L.n, kT2BM, N, kT2BN);
     const size_t pbytes = p.nsplit > 1 ? (size_t)p.n_rb * p.nsplit * N * kT2BM * 4 : 0;
     L.planned_nsplit = p.nsplit;
     if (L.plan_only) {
