@@ -42,6 +42,7 @@ N_PROBES = 16
 EPS_T = 1e-4
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
+EX2_PEAK_TENTRIES = 152 * 32 * 2.070e9 / 1e12            # SMs x ex2 per clock x max clock
 WORK_FILE = os.path.join(ROOT, "profiles", "census_like_step_work.txt")
 GRAD_ERROR_FILE = os.path.join(ROOT, "profiles", "grad_error_census_like.txt")
 # per K V kernel: its ncu traffic summary and the sources whose hash it was taken for
@@ -487,24 +488,50 @@ def run_ours(args):
     if tf and tf.get("kmv_source_hash") == kmv_source_hash(kkey):
         traffic = float(tf["dram_bytes_per_launch"])
     kmv_tflops = prof["kmv_tflops"]
-    roofline = {
-        "bound": "alu",
-        "kernel": name,
-        "achieved": kmv_tflops,
-        "peak": FP32_FMA_PEAK_TFLOPS,
-        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz max SM clock",
-        "unit": "TFLOP/s",
-        "frac": (kmv_tflops / FP32_FMA_PEAK_TFLOPS) if kmv_tflops else None,
-        "traffic": traffic,
-        "flop_per_entry": "3d + 2 + 2R (distance, kernel value, contraction)",
+    kmv_s = prof["kmv_ms"] / 1e3
+    flop_view = {"unit": "TFLOP/s", "achieved": kmv_tflops, "peak": FP32_FMA_PEAK_TFLOPS,
+                 "frac": (kmv_tflops / FP32_FMA_PEAK_TFLOPS) if kmv_tflops else None,
+                 "flop_per_entry": "3d + 2 + 2R (distance, kernel value, contraction)",
+                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz"}
+    if kkey == "mixed_tensor":
+        # the cross term and the contraction run on the tensor cores; what every generated
+        # entry still needs on the CUDA cores is one exponential (ex2 on the XU pipe)
+        ent = prof["kmv_launches"] * float(n) * n / kmv_s if kmv_s > 0 else None
+        roofline = {
+            "bound": "alu",
+            "kernel": name,
+            "achieved": ent / 1e12 if ent else None,
+            "peak": EX2_PEAK_TENTRIES,
+            "unit": "T entries/s",
+            "frac": (ent / 1e12 / EX2_PEAK_TENTRIES) if ent else None,
+            "peak_source": "derived: 152 SMs x 32 ex2/clk (XU pipe) x 2070 MHz; one ex2 per "
+                           "generated kernel entry",
+            "traffic": traffic,
+            "fp32_equivalent_flops": flop_view,
+        }
+    else:
+        roofline = {
+            "bound": "alu",
+            "kernel": name,
+            "achieved": kmv_tflops,
+            "peak": FP32_FMA_PEAK_TFLOPS,
+            "peak_source": flop_view["peak_source"],
+            "unit": "TFLOP/s",
+            "frac": flop_view["frac"],
+            "traffic": traffic,
+            "flop_per_entry": flop_view["flop_per_entry"],
+        }
+    roofline.update({
+        "traffic_unit": "DRAM bytes per launch (ncu capture of the dominant instance; see its file)",
         "measured_in": "event-timed pass of %d steps (host loop, one event pair per launch)"
                        % prof["steps"],
         "kmv_launches": prof["kmv_launches"],
         "kmv_ms_per_round": prof["kmv_ms"] / prof["rounds"] if prof["rounds"] else None,
+        "kmv_ms_per_launch": prof["kmv_ms"] / prof["kmv_launches"] if prof["kmv_launches"] else None,
         "grad_ms_per_step": prof["grad_ms"] / prof["steps"],
         "grad_tflops": (prof["grad_flop"] / (prof["grad_ms"] / 1e3) / 1e12
                         if prof["grad_ms"] > 0 else None),
-    }
+    })
     grad_err = _kv_file(GRAD_ERROR_FILE)
     line = {
         "metric": "SGLD steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
