@@ -172,3 +172,31 @@ def test_dk_bilinear_argument_errors():
             ctx.dk_bilinear(np.array([0.0, np.inf, 0.0, 0.0, 0.0]), A, A)
         with pytest.raises(u.UlisseError):
             ctx.dk_bilinear(prob.psi_true, A, A, scale=[1.0, np.nan])
+
+
+@pytest.mark.parametrize("precision", [u.PREC_FP32, u.PREC_MIXED, u.PREC_FP64])
+def test_grad_is_solve_plus_bilinear_form(precision):
+    """ulisse_grad = the ULISSE solves of [y, probes] (Sec. 4, two estimators for y) followed
+    by the bilinear forms 1/2 a1^T dK a2 - 1/(2 N_r) sum_j z_j^T dK r_j (Eq. gradient:unbiased)
+    -- bit for bit, with the same step (same probes and truncation draws).  Pins the
+    gradient's factor maps and scales on every path."""
+    import oracle
+    oracle.build()
+    prob = w.census_like(n=3000, seed=4242)
+    psi = prob.psi_true + 0.2
+    nr, n = 8, prob.n
+    X = torch.from_numpy(prob.X).cuda()
+    y = torch.from_numpy(prob.y).cuda()
+    cfg = u.ulisse_config_default(n_probes=nr, precision=precision, seed=91)
+    with u.Context(X, y, cfg) as c:
+        for step in (0, 3):
+            g_api, _ = c.grad(psi, step=step)
+            R = oracle.probes(n, nr, 0, 91, step).astype(np.float32)
+            Bm = np.column_stack([prob.y, R]).astype(np.float32)
+            S, _ = c.solve(psi, torch.from_numpy(Bm).cuda(), n_est=[2] + [1] * nr, step=step)
+            S = S.cpu().numpy()
+            A = np.column_stack([S[:, 0], S[:, 2:]]).astype(np.float32)
+            B = np.column_stack([S[:, 1], R]).astype(np.float32)
+            s = np.array([0.5] + [-0.5 / nr] * nr)
+            g_man = c.dk_bilinear(psi, torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), s)
+            assert np.array_equal(g_api, g_man)
