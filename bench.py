@@ -190,6 +190,9 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------
 # oracle timing on the host cores (bounded sample, scaled to steps/s)
 # ----------------------------------------------------------------------------------------
+_ORACLE_CAL = {}   # per problem size: inputs and per-row times of the oracle (one calibration)
+
+
 def oracle_sample(prob, work, target_s, rng_seed=0):
     """Time the oracle's two O(n^2) kernels on a row sample of the full-size workload:
     K V with 17 right-hand sides (all n columns) and the all-parameter derivative products
@@ -197,24 +200,28 @@ def oracle_sample(prob, work, target_s, rng_seed=0):
     import numpy as np
 
     import oracle
-    oracle.build()
     n, d = prob.n, prob.d
-    Xd = prob.X.astype(np.float64)
-    rng = np.random.default_rng(rng_seed)
     R = 1 + N_PROBES
-    V = rng.standard_normal((n, R))
-    # calibrate on a few hundred rows (threads warm), then size the sample to the target
-    cores = oracle.omp_threads()
-    oracle.kmv_rows(Xd, prob.psi_true, V, np.arange(cores))
-    m0 = 8 * cores
-    t0 = time.perf_counter()
-    oracle.kmv_rows(Xd, prob.psi_true, V, np.arange(m0))
-    t_cal = max(time.perf_counter() - t0, 1e-4)
-    m_kv = int(max(m0, min(n, m0 * 0.6 * target_s / t_cal)))
-    t0 = time.perf_counter()
-    oracle.dkmv_all_rows(Xd, prob.psi_true, V, np.arange(2 * cores))
-    t_cal_g = max(time.perf_counter() - t0, 1e-4)
-    m_g = int(max(2 * cores, min(n, 2 * cores * 0.4 * target_s / t_cal_g)))
+    rng = np.random.default_rng(rng_seed)
+    cal = _ORACLE_CAL.get(n)
+    if cal is None:
+        # once per run: build, inputs, and a calibration on a few hundred rows (threads warm)
+        oracle.build()
+        Xd = prob.X.astype(np.float64)
+        V = np.random.default_rng(0).standard_normal((n, R))
+        cores = oracle.omp_threads()
+        oracle.kmv_rows(Xd, prob.psi_true, V, np.arange(cores))
+        m0 = 8 * cores
+        t0 = time.perf_counter()
+        oracle.kmv_rows(Xd, prob.psi_true, V, np.arange(m0))
+        t_row = max(time.perf_counter() - t0, 1e-4) / m0
+        t0 = time.perf_counter()
+        oracle.dkmv_all_rows(Xd, prob.psi_true, V, np.arange(2 * cores))
+        t_row_g = max(time.perf_counter() - t0, 1e-4) / (2 * cores)
+        cal = _ORACLE_CAL[n] = (Xd, V, cores, t_row, t_row_g)
+    Xd, V, cores, t_row, t_row_g = cal
+    m_kv = int(max(8 * cores, min(n, 0.6 * target_s / t_row)))
+    m_g = int(max(2 * cores, min(n, 0.4 * target_s / t_row_g)))
     rows = np.sort(rng.choice(n, m_kv, replace=False))
     t0 = time.perf_counter()
     oracle.kmv_rows(Xd, prob.psi_true, V, rows)
@@ -271,7 +278,7 @@ def run_reference(args):
     work = _work_from_file()
     if work is None:
         raise SystemExit("missing %s (per-step work of the workload)" % WORK_FILE)
-    per_step = max(2.0, args.cpu_seconds / max(args.steps, 1))
+    per_step = max(0.5, args.cpu_seconds / max(args.steps, 1))   # whole run: a minute or two
     for _ in range(args.warmup):
         oracle_sample(prob, work, per_step / 4)
     rates, host = [], 0.0
