@@ -287,27 +287,32 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
       const bool ready = t2_warp_wait(&c_full[lt % S::NCF], (uint32_t)((lt / S::NCF) & 1));
       if (!__all_sync(0xffffffffu, ready && !*s_fail)) { ok = false; break; }
       tc::fence_after();
+      // all 32 columns of C in one tensor-memory round trip; each pair's K high and low parts
+      // are written back into the pair's own registers (no extra registers live)
+      const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32);
+      uint32_t c[32];
+      tc::tmem_ld16x2(ccol, c);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        // the exponent is <= log2 sigma^2 up to rounding (about 1e-6 relative in k)
+        const float k0 = ex2_approx(ai + __uint_as_float(c[2 * q]));
+        const float k1 = ex2_approx(ai + __uint_as_float(c[2 * q + 1]));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
+        c[2 * q] = *reinterpret_cast<const uint32_t*>(&h);
+        c[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&l);
+      }
 #pragma unroll
       for (int hh = 0; hh < 2; ++hh) {
-        // columns [16 hh, 16 hh + 16): C read back, K written over them (high parts, then
-        // low parts: the A operand of the contraction's k-step hh)
-        const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32 + hh * 16);
-        float c[16];
-        tc::tmem_ld16(ccol, c);
-        uint32_t hi[8], lo[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          // the exponent is <= log2 sigma^2 up to rounding (about 1e-6 relative in k)
-          const float k0 = ex2_approx(ai + c[2 * q]);
-          const float k1 = ex2_approx(ai + c[2 * q + 1]);
-          const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
-          const float2 hf = __bfloat1622float2(h);
-          const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
-          hi[q] = *reinterpret_cast<const uint32_t*>(&h);
-          lo[q] = *reinterpret_cast<const uint32_t*>(&l);
-        }
-        tc::tmem_st8(ccol, hi);
-        tc::tmem_st8(ccol + 8, lo);
+        // columns [16 hh, 16 hh + 16): high parts, then low parts (the A operand of the
+        // contraction's k-step hh)
+        const uint32_t hi[8] = {c[16 * hh + 0], c[16 * hh + 2], c[16 * hh + 4], c[16 * hh + 6],
+                                c[16 * hh + 8], c[16 * hh + 10], c[16 * hh + 12], c[16 * hh + 14]};
+        const uint32_t lo[8] = {c[16 * hh + 1], c[16 * hh + 3], c[16 * hh + 5], c[16 * hh + 7],
+                                c[16 * hh + 9], c[16 * hh + 11], c[16 * hh + 13], c[16 * hh + 15]};
+        tc::tmem_st8(ccol + 16 * hh, hi);
+        tc::tmem_st8(ccol + 16 * hh + 8, lo);
       }
       tc::tmem_wait_st();
       tc::fence_before();
