@@ -258,6 +258,16 @@ def _work_from_file():
 # ----------------------------------------------------------------------------------------
 # distributed helpers (replicas)
 # ----------------------------------------------------------------------------------------
+def max_over_ranks(v, world, device):
+    """The largest of v over all ranks (the slowest rank's time); v itself with one rank."""
+    if world <= 1:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_setup(args, backend):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -418,19 +428,15 @@ def run_ours(args):
             tuned[key] = c.autotune(prob.psi_true, R, reps=3)
         return c
 
-    def max_over_ranks(v):
-        if world > 1:
-            t = torch.tensor([v], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            return float(t.item())
-        return v
+    def max_ranks(v):
+        return max_over_ranks(v, world, dev)
 
     # chosen path: the timed region
     warm = not args.no_warm
     ctx = make_ctx(args.path, args.refresh, warm, "chosen")
     res = _timed_steps(ctx, dev, stream, prob.psi_true, K, W, 0, flush, barrier,
                        ClockSampler(local))
-    total_ms = max_over_ranks(res["total_ms"])
+    total_ms = max_ranks(res["total_ms"])
     value = world * K / (total_ms / 1000.0)
     rounds, erhs, launches = res["counters"]
 
@@ -448,7 +454,7 @@ def run_ours(args):
     for k in range(K):
         psi_h, g_h = ctx.sgld_step(prob.psi_true.copy(), EPS_T, step=W + k)
     torch.cuda.synchronize(dev)
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_ranks(time.perf_counter() - t0)
     e2e_rounds = (ctx.counters()[0] - r_e0) / max(K, 1)
     e2e_value = world * K / e2e_s
     ctx.close()
@@ -460,7 +466,7 @@ def run_ours(args):
         ores = _timed_steps(octx, dev, stream, prob.psi_true, K, W, 0, flush, barrier)
         oprof = _profile_pass(octx, dev, prob.psi_true, args.profile_steps, 50_000, n, R)
         octx.close()
-        ototal = max_over_ranks(ores["total_ms"])
+        ototal = max_ranks(ores["total_ms"])
         return {"value": world * K / (ototal / 1000.0), "unit": "steps/s",
                 "ms_per_step": ototal / K,
                 "mvp_rounds_per_step": ores["counters"][0] / K,
