@@ -54,7 +54,11 @@ typedef enum {
 
 typedef enum {
     ULISSE_PREC_FP32 = 0,     /* FP32 vectors and SIMT products, FP64 scalar recurrences */
-    ULISSE_PREC_MIXED = 1,    /* tensor-core (tcgen05) products, FP32 vectors */
+    ULISSE_PREC_MIXED = 1,    /* tensor-core (tcgen05) products, FP32 vectors: K V with the
+                                 exponent's dot product by three TF32 products and the
+                                 contraction by three BF16 products, the gradient's bilinear
+                                 forms by three BF16 products; each result's error is stated
+                                 at the call (about 1e-4 of its dot-product scale at most) */
     ULISSE_PREC_FP64 = 2      /* FP64 everywhere (the paper's double-precision CMVPs) */
 } ulisse_precision;
 
@@ -119,7 +123,9 @@ ulisse_status ulisse_create_host(ulisse_ctx **out, const float *X, const float *
  *   V    device, n x R column-major (leading dimension n), R >= 1.
  *   U    device, n x R column-major; must not overlap V.
  * In FP64 precision V and U are read and written as float and converted; use
- * ulisse_kmv_f64 for double data.  Asynchronous on the context's stream.
+ * ulisse_kmv_f64 for double data.  In mixed precision K V (which == -1) runs on the tensor
+ * cores (each entry of U within 1e-4 of sum_j |K_ij| |V_jr|) and the derivative products in
+ * FP32.  Asynchronous on the context's stream.
  * Errors: ULISSE_ERR_ARG (which out of range, R < 1, null, non-finite psi).
  */
 ulisse_status ulisse_kmv(ulisse_ctx *ctx, const double *psi, int which, const float *V, int R,
