@@ -152,6 +152,32 @@ def test_kmv_mixed_full_size_sampled_rows(orc, cross):
     assert comp <= MIXED_TOL
 
 
+@pytest.fixture(scope="module")
+def near_dup_full():
+    return w.near_duplicates()
+
+
+@pytest.mark.parametrize("cross", CROSS)
+def test_kmv_mixed_near_duplicates_full_size(orc, near_dup_full, cross):
+    """The near-duplicate workload at its full size (n = 200,000, d = 16, 64 right-hand sides,
+    1% jittered copies): 32 sampled rows against the oracle.  At this n the accumulation
+    bound gives every row block at least ten j-splits (the split partial sums take ~0.5 GB)."""
+    prob = near_dup_full
+    n = prob.n
+    rng = np.random.default_rng(12)
+    V = rng.choice([-1.0, 1.0], (n, 64)).astype(np.float32)
+    rows = np.sort(rng.choice(n, 32, replace=False))
+    with _ctx(prob, precision=u.PREC_MIXED, tc_cross_term=cross) as ctx:
+        Ug = ctx.kmv(prob.psi_true, torch.from_numpy(V).cuda()).cpu().numpy()[rows]
+    Xd, Vd = prob.X.astype(np.float64), V.astype(np.float64)
+    ref = orc.kmv_rows(Xd, prob.psi_true, Vd, rows)
+    scale = orc.kmv_rows(Xd, prob.psi_true, Vd, rows, absolute=True)
+    comp = np.max(np.abs(Ug - ref) / scale)
+    print("mixed K V (cross %d) near-duplicates full size n=%d: max |err|/scale %.2e"
+          % (cross, n, comp))
+    assert comp <= MIXED_TOL
+
+
 def test_kmv_symmetry_and_linearity():
     """Properties that hold at any size: e_i^T K e_j = e_j^T K e_i; K (aV) = a K V."""
     prob = w.random_problem(5000, 4, seed=9)
