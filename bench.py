@@ -553,8 +553,10 @@ def run_ours(args):
         "dtype": "bf16x3/f32" if args.path == "mixed" else "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "d": d, "n_probes": N_PROBES, "q": 1.0,
                    "beta": 1.0, "eps_t": EPS_T,
-                   "path": ("tcgen05 mixed K V (FP32 kernel values, 3xBF16 contraction)"
-                            if args.path == "mixed" else "fp32 SIMT K V"),
+                   "path": ("tcgen05 mixed precision: K V with the exponent's dot product "
+                            "by 3xTF32 and the contraction by 3xBF16, gradient pass by 3xBF16, "
+                            "FP32 accumulation"
+                            if args.path == "mixed" else "fp32 SIMT K V and gradient"),
                    "step_form": "host loop" if args.no_graph else "one CUDA graph launch per step",
                    "probe_refresh": args.refresh, "warm_started_solves": warm,
                    "steps_start_at": "the generating parameters (own step number each)",
