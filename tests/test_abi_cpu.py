@@ -49,7 +49,7 @@ def test_config_default(lib):
 
 @pytest.mark.parametrize("n,d,bad_cfg", [(0, 2, None), (10, 0, None), (10, 17, None),
                                          (10, 2, "n_probes"), (10, 2, "beta"),
-                                         (10, 2, "q"), (10, 2, "refresh")])
+                                         (10, 2, "q"), (10, 2, "refresh"), (10, 2, "cross")])
 def test_create_rejects_bad_arguments(lib, n, d, bad_cfg):
     from paper_1501_05427_gb300 import ulisse
     cfg = ulisse.ulisse_config_default()
@@ -61,6 +61,8 @@ def test_create_rejects_bad_arguments(lib, n, d, bad_cfg):
         cfg.q = float("nan")
     elif bad_cfg == "refresh":
         cfg.probe_refresh = 0
+    elif bad_cfg == "cross":
+        cfg.tc_cross_term = 3
     X = np.zeros((max(n, 1), max(d, 1)), np.float32)
     y = np.zeros(max(n, 1), np.float32)
     h = ctypes.c_void_p()
@@ -78,6 +80,7 @@ def test_null_pointers_rejected(lib):
     assert lib.ulisse_create(ctypes.byref(h), None, None, 10, 2, ctypes.byref(cfg), None) == 1
     assert lib.ulisse_kmv(None, None, -1, None, 1, None) == ulisse.ULISSE_ERR_ARG
     assert lib.ulisse_grad(None, None, 0, None, None) == ulisse.ULISSE_ERR_ARG
+    assert lib.ulisse_dk_bilinear(None, None, None, None, 1, None, None) == ulisse.ULISSE_ERR_ARG
     lib.ulisse_destroy(None)
 
 
