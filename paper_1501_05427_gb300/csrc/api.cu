@@ -478,8 +478,21 @@ static ulisse_status read_status(ulisse_ctx* ctx, int* status) {
   return ULISSE_OK;
 }
 
+// A CTA whose bounded wait ran out returns before it counts itself in its row block's split
+// counter or the gradient's last-CTA counter (both reset themselves only when every CTA
+// arrives): zero them, so that the context's next launches pick their last CTA correctly.
+static void reset_counters_after_timeout(ulisse_ctx* ctx) {
+  if (ctx->counters && ctx->counters_len > 0)
+    cudaMemsetAsync(ctx->counters, 0, sizeof(int) * ctx->counters_len, ctx->stream);
+  if (ctx->gcounter) cudaMemsetAsync(ctx->gcounter, 0, sizeof(int), ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+}
+
 static ulisse_status status_to_result(ulisse_ctx* ctx, int s) {
-  if (s & kStatusTimeout) return fail(ctx, ULISSE_ERR_TIMEOUT, "a bounded device wait ran out");
+  if (s & kStatusTimeout) {
+    reset_counters_after_timeout(ctx);
+    return fail(ctx, ULISSE_ERR_TIMEOUT, "a bounded device wait ran out");
+  }
   if (s & kStatusBadM) return fail(ctx, ULISSE_ERR_ARG, "M is not positive definite");
   if (s & kStatusBreakdown)
     return fail(ctx, ULISSE_ERR_BREAKDOWN, "CG breakdown (d^T K d <= 0 or non-finite)");
