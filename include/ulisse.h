@@ -450,6 +450,16 @@ typedef struct {
 ulisse_status ulisse_autotune(ulisse_ctx *ctx, const double *psi, int max_cols, int reps,
                               ulisse_tune_entry *out);
 
+/*
+ * Self-test of the failure path (no GPU fault is involved): one CTA waits on an mbarrier
+ * that nothing completes.  The wait gives up after about half a second (2^30 SM cycles), the
+ * kernel records the timeout in the context's status word as every kernel of the library
+ * does when one of its bounded waits runs out, and this call reports it as any call would:
+ * ULISSE_ERR_TIMEOUT (after zeroing the context's split counters, as every timeout does).
+ * The context stays usable.  Synchronises the stream.
+ */
+ulisse_status ulisse_selftest_wait_timeout(ulisse_ctx *ctx);
+
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);
 

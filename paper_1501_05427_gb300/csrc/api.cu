@@ -2493,6 +2493,32 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
   return ULISSE_OK;
 }
 
+// One CTA waits on an mbarrier that expects two arrivals and gets one: the wait, bounded by
+// the SM clock here (2^30 cycles, about half a second), runs out and the timeout is recorded
+// in the status word as every kernel records it.
+__global__ void selftest_wait_timeout_kernel(int* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    fence_barrier_init();
+    mbar_arrive_expect_tx(&bar, 0);   // one arrival (no bytes) of the two it waits for
+    bool done = false;
+    const long long t0 = clock64();
+    while (!done && clock64() - t0 < (1LL << 30)) done = mbar_try_wait(&bar, 0);
+    if (!done) atomicOr(status, kStatusTimeout);
+  }
+}
+
+ulisse_status ulisse_selftest_wait_timeout(ulisse_ctx* ctx) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  selftest_wait_timeout_kernel<<<1, 32, 0, ctx->stream>>>(ctx->status_dev);
+  CK(cudaGetLastError());
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
 ulisse_status ulisse_counters(const ulisse_ctx* ctx, long long* mvp_rounds, double* entry_rhs,
                               long long* kernel_launches) {
   if (!ctx) return ULISSE_ERR_ARG;

@@ -35,6 +35,7 @@ EXPORTED = [
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
     "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
+    "ulisse_selftest_wait_timeout",
 ]
 
 
@@ -118,6 +119,7 @@ def load():
     lib.ulisse_solve.argtypes = [P, P, P, I, P, P, P, U64, sp]
     lib.ulisse_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_dk_bilinear.argtypes = [P, P, P, P, I, P, P]
+    lib.ulisse_selftest_wait_timeout.argtypes = [P]
     lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
     lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
     lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
@@ -365,6 +367,10 @@ class Context:
         psi = _f64_host(psi, self.p)
         self._check(self._lib.ulisse_autotune(self._h, _hptr(psi), max_cols, reps, out))
         return [{k: getattr(e, k) for k, _ in ulisse_tune_entry._fields_} for e in out]
+
+    def selftest_wait_timeout(self):
+        """Run the failure-path self-test; returns the status code (ULISSE_ERR_TIMEOUT)."""
+        return self._lib.ulisse_selftest_wait_timeout(self._h)
 
     def set_graph(self, enable=True):
         """sgld_chain: one CUDA-graph launch per step (True) or the host loop (False)."""

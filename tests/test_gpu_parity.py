@@ -483,3 +483,20 @@ def test_bad_psi_rejected():
         assert ei.value.status == u.ULISSE_ERR_ARG
         with pytest.raises(u.UlisseError):
             ctx.kmv(prob.psi_true, torch.zeros((100, 1), device="cuda"), which=9)
+
+
+def test_timeout_path_leaves_context_usable():
+    """Failure detection without a GPU fault: a wait that nothing completes runs out, the
+    call returns ULISSE_ERR_TIMEOUT, and the same context then computes K V exactly as a
+    fresh context does."""
+    prob = w.random_problem(3000, 4, seed=88)
+    V = torch.randn((prob.n, 5), device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    with _ctx(prob) as fresh:
+        ref = fresh.kmv(prob.psi_true, V).cpu().numpy()
+    with _ctx(prob) as ctx:
+        ctx.kmv(prob.psi_true, V)
+        assert ctx.selftest_wait_timeout() == u.ULISSE_ERR_TIMEOUT
+        U = ctx.kmv(prob.psi_true, V).cpu().numpy()
+        g, _ = ctx.grad(prob.psi_true, step=0)
+    assert np.array_equal(U, ref)
+    assert np.all(np.isfinite(g))
