@@ -33,6 +33,7 @@ a wrong sign or index, a transposed operand, a wrong weight) fails at least one 
                         stationary moments of a Gaussian target
   cross_signal          sub-block of cov_matrix (signal part) for a subset of the inputs
   mlp.residual_matrices y_I - M c equals the rows I of y - K s_0 with dense K
+  mlp.forward           a two-unit network evaluated by hand (tanh ln a = (a^2-1)/(a^2+1))
   mlp.loss_and_grad     central finite differences of the loss in every parameter block;
                         the loss at a hand-built exact fit is 0, the ridge term alone
   mlp.pooled_constant   the loss gradient in b3 vanishes there (W3 = 0), and any other
@@ -698,3 +699,35 @@ def test_mlp_pooled_constant_is_the_loss_minimiser(orc):
     for _ in range(5):
         w1 = mlp.flatten([W1, b1, W2, b2, np.zeros_like(W3), c + 0.01 * rng.standard_normal(5)])
         assert mlp.loss_and_grad(w1, Psi, Rows, X, y, Z, mu, sd, hidden, ridge, M=M)[0] > loss
+
+
+def test_mlp_forward_hand_evaluated():
+    """mlp.forward on a network small enough to evaluate by hand.  With p = 2, H = 2, A = 2,
+    mu = (3, -1), sd = (2, 4) and psi = (5, -1) the standardised input is z = (1, 0).  W1's
+    first row (ln 2, ln 3) and b1 = 0 give h1 = (tanh ln 2, tanh ln 3) = (3/5, 4/5) (tanh ln a
+    = (a^2 - 1)/(a^2 + 1)); W1's second row (5, 7) is multiplied by z_2 = 0.  W2 = I and
+    b2 = (ln 2 - 3/5, ln 3 - 4/5) give h2 = (3/5, 4/5) again.  W3 = [[2, 1/2], [-1, 1]] and
+    b3 = (1/4, -1) give c = (6/5 - 4/5 + 1/4, 3/10 + 4/5 - 1) = (0.65, 0.1).  Dropping the
+    standardisation (z = psi), a tanh, or transposing W1 or W3 changes c."""
+    from oracle import mlp
+    ln2, ln3 = math.log(2.0), math.log(3.0)
+    W1 = np.array([[ln2, ln3], [5.0, 7.0]])
+    b1 = np.zeros(2)
+    W2 = np.eye(2)
+    b2 = np.array([ln2 - 0.6, ln3 - 0.8])
+    W3 = np.array([[2.0, 0.5], [-1.0, 1.0]])
+    b3 = np.array([0.25, -1.0])
+    w = mlp.flatten([W1, b1, W2, b2, W3, b3])
+    mu, sd = np.array([3.0, -1.0]), np.array([2.0, 4.0])
+    C, (Z, H1, H2) = mlp.forward(w, np.array([[5.0, -1.0]]), mu, sd, 2, 2, 2)
+    assert np.allclose(Z, [[1.0, 0.0]], rtol=0, atol=1e-15)
+    assert np.allclose(H1, [[0.6, 0.8]], rtol=0, atol=1e-15)
+    assert np.allclose(H2, [[0.6, 0.8]], rtol=0, atol=1e-15)
+    assert np.allclose(C, [[0.65, 0.1]], rtol=0, atol=1e-14)
+    # a second input, z = (0, 1): h1 = tanh(W1[1]) = (tanh 5, tanh 7)
+    C2, (_, H1b, H2b) = mlp.forward(w, np.array([[3.0, 3.0]]), mu, sd, 2, 2, 2)
+    t5, t7 = math.tanh(5.0), math.tanh(7.0)
+    assert np.allclose(H1b, [[t5, t7]], rtol=0, atol=1e-15)
+    h2 = np.tanh(np.array([t5 + ln2 - 0.6, t7 + ln3 - 0.8]))
+    assert np.allclose(C2[0], [2 * h2[0] - h2[1] + 0.25, 0.5 * h2[0] + h2[1] - 1.0],
+                       rtol=0, atol=1e-14)
