@@ -9,10 +9,17 @@ C ABI.  Prints one JSON line (rank 0).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 The headline is the chosen path -- tensor-core (tcgen05) mixed-precision K V, every step one
-CUDA-graph launch -- in SGLD steps/s; the plain FP32 path (SIMT K V, same graph form) is timed
-the same way beside it, and both report K V entry*RHS/s from an event-timed pass.  The
-gradient error of both paths at the same parameters is the committed measurement in
-profiles/grad_error_census_like.txt (tests/test_gpu_grad_error.py).
+CUDA-graph launch, probes reused for 20 steps with warm-started solves -- in SGLD steps/s;
+the plain FP32 path (SIMT K V, same graph form) is timed the same way beside it, and both
+report K V entry*RHS/s from an event-timed pass.  The roofline of the dominant K V kernel
+counts the method's work (n(n+1)/2 distinct exponentials per product) against the
+exponential unit's rate measured on the device in the same run.
+
+At N = 1 the same line carries the other configurations as keys: the gradient error of the
+paths (Sec. 5's measure, dense FP64 Cholesky reference on the device), the near-duplicate
+K V at full size (n = 200,000, d = 16, 64 RHS) with its error against oracle rows, the
+64-problem uneven batch, and the 2-D FP64 100-step chain beside the oracle's full chain
+(--no-extras skips them).
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a bounded sample of
 the same workload, scaled to SGLD steps/s).  With N > 1 (torchrun) every rank runs an
@@ -33,6 +40,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -42,9 +51,8 @@ N_PROBES = 16
 EPS_T = 1e-4
 L2_FLUSH_BYTES = 512 << 20          # > 129 MB L2: written between timed steps
 FP32_FMA_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x 2 x max clock
-EX2_PEAK_TENTRIES = 152 * 32 * 2.070e9 / 1e12            # SMs x ex2 per clock x max clock
+EX2_PEAK_DERIVED_TENTRIES = 152 * 32 * 2.070e9 / 1e12    # SMs x ex2 per clock x max clock
 WORK_FILE = os.path.join(ROOT, "profiles", "census_like_step_work.txt")
-GRAD_ERROR_FILE = os.path.join(ROOT, "profiles", "grad_error_census_like.txt")
 # per K V kernel: its ncu traffic summary and the sources whose hash it was taken for
 KMV_KERNELS = {
     "fp32": ("kmv_kernel (tile-generating K V, FP32 SIMT)",
@@ -70,6 +78,11 @@ KMV_KERNELS = {
                       "paper_1501_05427_gb300/csrc/ulisse_internal.cuh"]),
 }
 CROSS_KEY = {1: "mixed_pipe", 2: "mixed_tensor"}
+
+
+def generated_entries(n):
+    """Covariance entries the tensor-core K V kernel generates per launch (every (i, j))."""
+    return float(n) * n
 
 
 def kernel_key(path, tune_table=None, live_cols=None):
@@ -108,6 +121,13 @@ def parse_args():
                     help="chosen path: start every solve from zero (no warm-started solves)")
     ap.add_argument("--profile-steps", type=int, default=8,
                     help="steps of the event-timed pass (per-launch K V times)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the other configurations' keys (gradient error, near-duplicate "
+                         "K V, uneven batch, 2-D FP64 chain)")
+    ap.add_argument("--c3-rows", type=int, default=4000,
+                    help="output rows of the near-duplicate K V the oracle evaluates")
+    ap.add_argument("--grad-reps", type=int, default=100,
+                    help="repetitions of the gradient-error measurement")
     return ap.parse_args()
 
 
@@ -307,7 +327,13 @@ def run_reference(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": prob.n, "d": prob.d, "n_probes": N_PROBES},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": rates[-1]["cores"],
-                         "kind": "oracle", "sample": rates[-1]["sample"]},
+                         "kind": "oracle", "sample": rates[-1]["sample"],
+                         "extrapolated": True},
+        "extrapolated": True,
+        "extrapolation": ("each step is a timed sample of the oracle's two O(n^2) routines on "
+                          "a row subset of the full workload, scaled by n/m and by the "
+                          "chosen GPU path's work per step; no full step of the oracle runs "
+                          "(one would take minutes)"),
         "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "wall_s": wall,
@@ -391,6 +417,223 @@ def _profile_pass(ctx, dev, psi0, P, step_base, n, R):
     }
 
 
+# ----------------------------------------------------------------------------------------
+# the other configurations (keys of the same line; rank 0 at N = 1)
+# ----------------------------------------------------------------------------------------
+def _exact_gradient_torch(X, y, psi, dev):
+    """g_i = -1/2 Tr(K^-1 dK_i) + 1/2 y^T K^-1 dK_i K^-1 y in FP64 on the device (dense
+    Cholesky through torch.linalg): the reference of the gradient-error measurement, n a few
+    thousand.  Parameters psi = (log l_1..log l_d, log sigma^2, log lambda)."""
+    import torch
+    Xt = torch.from_numpy(X).to(dev, torch.float64)
+    yt = torch.from_numpy(y).to(dev, torch.float64)
+    n, d = Xt.shape
+    ell = torch.tensor(psi[:d], dtype=torch.float64, device=dev).exp()
+    s2, lam = math.exp(psi[d]), math.exp(psi[d + 1])
+    Xs = Xt / ell
+    diff2 = [(Xs[:, k, None] - Xs[None, :, k]) ** 2 for k in range(d)]
+    Ks = s2 * torch.exp(-0.5 * sum(diff2))
+    K = Ks + lam * torch.eye(n, dtype=torch.float64, device=dev)
+    L = torch.linalg.cholesky(K)
+    Kinv = torch.cholesky_inverse(L)
+    a = torch.cholesky_solve(yt[:, None], L)[:, 0]
+    g = []
+    for dK in [Ks * diff2[k] for k in range(d)] + [Ks]:
+        g.append(float(-0.5 * torch.sum(Kinv * dK) + 0.5 * a @ (dK @ a)))
+    g.append(float(-0.5 * lam * torch.trace(Kinv) + 0.5 * lam * (a @ a)))
+    return np.array(g)
+
+
+def grad_error_leg(dev, stream, reps):
+    """Sec. 5's gradient error ||g - g~||^2 / ||g||^2 over `reps` seeded repetitions on a
+    Census-shaped problem small enough for a dense Cholesky (n = 4,000, 16 probes), at the
+    generating parameters + 0.3 (where ||g|| is not ~0).  Paths: plain FP32 (probes redrawn
+    every step, cold solves), mixed (tensor cores, same options) and the chosen form (mixed,
+    probes reused for 20 steps, warm-started solves); same seeds on every path."""
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+    prob = w.census_like(n=4000, seed=20150124)
+    psi = prob.psi_true + 0.3
+    t0 = time.perf_counter()
+    g = _exact_gradient_torch(prob.X, prob.y, psi, dev)
+    t_exact = time.perf_counter() - t0
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    out = {"statistic": "||g - g~||^2 / ||g||^2 over %d seeded repetitions, census_like "
+                        "n=4000, 16 probes, q=1, psi = truth + 0.3" % reps,
+           "g_norm": float(np.linalg.norm(g)),
+           "reference": "dense FP64 Cholesky on the device (%.1f s)" % t_exact}
+    legs = (("plain_fp32", u.PREC_FP32, 1, 0), ("mixed", u.PREC_MIXED, 1, 0),
+            ("chosen", u.PREC_MIXED, 20, 1))
+    for name, prec, refresh, warm in legs:
+        cfg = u.ulisse_config_default(n_probes=16, precision=prec, seed=77,
+                                      probe_refresh=refresh, warm_start_probes=warm,
+                                      max_iter=1000)
+        errs, rounds = [], []
+        with u.Context(X, y, cfg, stream=stream) as ctx:
+            for k in range(reps):
+                r0 = ctx.counters()[0]
+                gk, _ = ctx.grad(psi, step=k, allow=(u.ULISSE_ERR_MAXITER,))
+                rounds.append(ctx.counters()[0] - r0)
+                errs.append(float(np.sum((gk - g) ** 2) / np.sum(g * g)))
+        e = np.array(errs)
+        r = float(np.mean(rounds))
+        out[name] = {"mean": float(e.mean()), "se": float(e.std(ddof=1) / math.sqrt(len(e))),
+                     "median": float(np.median(e)), "p90": float(np.percentile(e, 90)),
+                     "mvp_rounds_per_step": r,
+                     # averaging m independent unbiased estimates divides the error by m at
+                     # m times the rounds, so error x rounds is the cost of a given error
+                     "median_x_rounds": float(np.median(e)) * r,
+                     "p90_x_rounds": float(np.percentile(e, 90)) * r}
+    base = out["plain_fp32"]
+    out["rounds_at_equal_error_plain_over"] = {
+        k: {"median": base["median_x_rounds"] / out[k]["median_x_rounds"],
+            "p90": base["p90_x_rounds"] / out[k]["p90_x_rounds"]} for k in ("mixed", "chosen")}
+    return out
+
+
+def _event_time(fn, stream, flush, reps, warm=2):
+    """Median CUDA-event time (ms) of fn() on `stream`, L2 flushed before each launch."""
+    import torch
+    for _ in range(warm):
+        fn()
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def near_duplicates_leg(dev, stream, flush, rows_oracle):
+    """K V at the near-duplicate workload's full size (n = 200,000, d = 16, 1% jittered
+    copies, 64 right-hand sides): entry-RHS/s of the tensor-core path and of the FP32 SIMT
+    path, and their error against the FP64 oracle on `rows_oracle` sampled output rows (the
+    oracle's time for those rows is its CPU baseline at this size)."""
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+    prob = w.near_duplicates()
+    n, d, R = prob.n, prob.d, 64
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    V = torch.from_numpy(np.random.default_rng(64).standard_normal((n, R)).astype(np.float32))
+    Vd = V.to(dev).t().contiguous().t()          # column-major, as the library takes it
+    out = {"workload": "near_duplicates", "n": n, "d": d, "rhs": R,
+           "duplicates": int(prob.meta["duplicates"])}
+    res = {}
+    for name, prec in (("mixed", u.PREC_MIXED), ("fp32", u.PREC_FP32)):
+        cfg = u.ulisse_config_default(precision=prec, n_probes=16)
+        with u.Context(X, y, cfg, stream=stream) as ctx:
+            U = torch.empty((R, n), dtype=torch.float32, device=dev).t()
+            ms = _event_time(lambda: ctx.kmv(prob.psi_true, Vd, out=U), stream, flush, 5)
+            res[name] = U.cpu().numpy()
+        out[name] = {"ms_per_launch": ms, "entry_rhs_per_s": float(n) * n * R / (ms / 1e3)}
+    out["speedup_mixed_over_fp32"] = out["fp32"]["ms_per_launch"] / out["mixed"]["ms_per_launch"]
+    if rows_oracle > 0:
+        import oracle
+        oracle.build()
+        rows = np.sort(np.random.default_rng(7).choice(n, rows_oracle, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.kmv_rows(prob.X.astype(np.float64), prob.psi_true,
+                              V.numpy().astype(np.float64), rows)
+        t_orc = time.perf_counter() - t0
+        for name in ("mixed", "fp32"):
+            Ur = res[name][rows].astype(np.float64)
+            out[name]["error_vs_oracle"] = {
+                "rows": int(rows_oracle),
+                "frobenius_rel": float(np.linalg.norm(Ur - ref) / np.linalg.norm(ref)),
+                "max_col_rel": float(np.max(np.linalg.norm(Ur - ref, axis=0) /
+                                            np.linalg.norm(ref, axis=0))),
+                "max_abs_over_max_ref": float(np.max(np.abs(Ur - ref)) / np.max(np.abs(ref)))}
+        out["cpu_baseline"] = {"value": rows_oracle * float(n) * R / t_orc,
+                               "unit": "entry·RHS/s", "cores": oracle.omp_threads(),
+                               "kind": "oracle", "extrapolated": False,
+                               "sample": "oracle K V of %d output rows against all %d inputs, "
+                                         "64 RHS, %.1f s" % (rows_oracle, n, t_orc)}
+    return out
+
+
+def small_2d_leg(dev, stream, n_steps=100):
+    """The 2-D FP64 configuration: n = 1,000, 4 Gaussian probes, 100 SGLD steps at step size
+    1e-4 from the generating parameters, as one chain (one graph launch per step) on the FP64
+    and the FP32 path, and the oracle's full 100-step chain on the host cores (timed, not
+    extrapolated)."""
+    import torch
+
+    import oracle
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+    prob = w.small_2d()
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    p = prob.d + 2
+    out = {"workload": "small_2d", "n": prob.n, "d": prob.d, "n_probes": 4,
+           "probe_kind": "gaussian", "steps": n_steps, "eps_t": 1e-4}
+    finals = {}
+    for name, prec in (("fp64", u.PREC_FP64), ("fp32", u.PREC_FP32)):
+        cfg = u.ulisse_config_default(precision=prec, n_probes=4, probe_kind=u.PROBE_GAUSSIAN,
+                                      q=1.0, beta=1.0, max_iter=2000, seed=20150122)
+        with u.Context(X, y, cfg, stream=stream) as ctx:
+            eps = torch.full((n_steps,), 1e-4, dtype=torch.float64, device=dev)
+            psi = torch.tensor(prob.psi_true, dtype=torch.float64, device=dev)
+            ctx.sgld_chain(psi, eps[:5], step0=10_000)          # warm-up (graph build)
+            psi.copy_(torch.tensor(prob.psi_true, dtype=torch.float64))
+            r0 = ctx.counters()[0]
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            ctx.sgld_chain(psi, eps, step0=0, allow=(u.ULISSE_ERR_MAXITER,))
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b)
+            # the same chain again with its trace (outside the timed span)
+            trace = torch.zeros((n_steps, p), dtype=torch.float64, device=dev)
+            psi.copy_(torch.tensor(prob.psi_true, dtype=torch.float64))
+            ctx.sgld_chain(psi, eps, step0=0, trace_dev=trace, allow=(u.ULISSE_ERR_MAXITER,))
+            finals[name] = trace.cpu().numpy()
+            out[name] = {"steps_per_s": n_steps / (ms / 1e3), "ms_per_step": ms / n_steps,
+                         "mvp_rounds_per_step": (ctx.counters()[0] - r0) / n_steps}
+    oracle.build()
+    Xd, yd = prob.X.astype(np.float64), prob.y.astype(np.float64)
+    psi = prob.psi_true.copy()
+    orc_trace = []
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        psi, _, _ = oracle.sgld_step(Xd, yd, psi, 1e-4, nr=4, probe_kind=1, q=1.0, beta=1.0,
+                                     max_iter=2000, seed=20150122, step=k)
+        orc_trace.append(psi)
+    t_orc = time.perf_counter() - t0
+    orc_trace = np.array(orc_trace)
+    out["cpu_baseline"] = {"value": n_steps / t_orc, "unit": "steps/s",
+                           "cores": oracle.omp_threads(), "kind": "oracle",
+                           "extrapolated": False,
+                           "sample": "the oracle's full %d-step chain (%.1f s)" % (n_steps, t_orc)}
+    # the chains run the same draws; the FP64 one follows the oracle's chain until rounding
+    # flips a discrete decision (an early stop near its threshold) on an ill-conditioned solve
+    track = {}
+    for k, tr in finals.items():
+        dif = np.max(np.abs(tr - orc_trace), axis=1)
+        off = np.nonzero(dif > 1e-6)[0]
+        track[k] = {"steps_within_1e-6": int(off[0]) if len(off) else n_steps,
+                    "max_abs_diff_first_10": float(dif[:10].max()),
+                    "final_max_abs_diff": float(dif[-1])}
+    out["psi_vs_oracle_chain"] = track
+    return out
+
+
+def uneven_batch_leg(args, dev, stream, flush, K=5, W=2):
+    """The 64-problem uneven batch, one graph launch per batched step (see run_batch)."""
+    return _batch_measure(args, dev, stream, flush, K, W, sampler=None)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -430,6 +673,9 @@ def run_ours(args):
 
     def max_ranks(v):
         return max_over_ranks(v, world, dev)
+
+    # the exponential unit's throughput on this device (the mixed path's roofline)
+    ex2_rate, ex2_ms = u.ulisse_measure_ex2_rate(stream, reps=20)
 
     # chosen path: the timed region
     warm = not args.no_warm
@@ -500,25 +746,39 @@ def run_ours(args):
     tf = _kv_file(traffic_file)
     if tf and tf.get("kmv_source_hash") == kmv_source_hash(kkey):
         traffic = float(tf["dram_bytes_per_launch"])
-    kmv_tflops = prof["kmv_tflops"]
     kmv_s = prof["kmv_ms"] / 1e3
-    flop_view = {"unit": "TFLOP/s", "achieved": kmv_tflops, "peak": FP32_FMA_PEAK_TFLOPS,
-                 "frac": (kmv_tflops / FP32_FMA_PEAK_TFLOPS) if kmv_tflops else None,
-                 "flop_per_entry": "3d + 2 + 2R (distance, kernel value, contraction)",
+    launches_kv = prof["kmv_launches"]
+    # algorithmic work per K V launch (the method's, Sec. 3): k_ij = k_ji, so n(n+1)/2
+    # distinct kernel values (distance and exponential), and the n^2 R multiply-adds of the
+    # contraction
+    distinct = float(n) * (n + 1) / 2.0
+    alg_flop = launches_kv * (distinct * (3.0 * d + 2.0) + 2.0 * R * float(n) * n)
+    alg_tflops = alg_flop / kmv_s / 1e12 if kmv_s > 0 else None
+    flop_view = {"unit": "TFLOP/s", "achieved": alg_tflops, "peak": FP32_FMA_PEAK_TFLOPS,
+                 "frac": (alg_tflops / FP32_FMA_PEAK_TFLOPS) if alg_tflops else None,
+                 "flop_per_launch": "n(n+1)/2 (3d + 2) + 2 R n^2 (distinct kernel values, "
+                                    "contraction)",
                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz"}
+    ex2_peak = ex2_rate / 1e12
     if kkey == "mixed_tensor":
-        # the cross term and the contraction run on the tensor cores; what every generated
-        # entry still needs on the CUDA cores is one exponential (ex2 on the XU pipe)
-        ent = prof["kmv_launches"] * float(n) * n / kmv_s if kmv_s > 0 else None
+        # the cross term and the contraction run on the tensor cores; what every kernel value
+        # still needs on the CUDA cores is one exponential (ex2 on the XU pipe)
+        exps = launches_kv * distinct / kmv_s if kmv_s > 0 else None
+        gen = launches_kv * generated_entries(n) / kmv_s if kmv_s > 0 else None
         roofline = {
             "bound": "alu",
             "kernel": name,
-            "achieved": ent / 1e12 if ent else None,
-            "peak": EX2_PEAK_TENTRIES,
-            "unit": "T entries/s",
-            "frac": (ent / 1e12 / EX2_PEAK_TENTRIES) if ent else None,
-            "peak_source": "derived: 152 SMs x 32 ex2/clk (XU pipe) x 2070 MHz; one ex2 per "
-                           "generated kernel entry",
+            "achieved": exps / 1e12 if exps else None,
+            "peak": ex2_peak,
+            "unit": "T exp/s",
+            "frac": (exps / 1e12 / ex2_peak) if exps else None,
+            "work_per_launch": "n(n+1)/2 exponentials (the distinct kernel values; k_ij = "
+                               "k_ji), n = %d" % n,
+            "peak_source": "measured: ulisse_measure_ex2_rate, best of 20 launches of "
+                           "independent ex2.approx.ftz.f32 on every SM (%.3f ms); derived "
+                           "152 x 32/clk x 2070 MHz = %.2f" % (ex2_ms, EX2_PEAK_DERIVED_TENTRIES),
+            "generated_entries_per_s": gen / 1e12 if gen else None,
+            "generated_entries_per_launch": generated_entries(n),
             "traffic": traffic,
             "fp32_equivalent_flops": flop_view,
         }
@@ -526,13 +786,14 @@ def run_ours(args):
         roofline = {
             "bound": "alu",
             "kernel": name,
-            "achieved": kmv_tflops,
+            "achieved": alg_tflops,
             "peak": FP32_FMA_PEAK_TFLOPS,
             "peak_source": flop_view["peak_source"],
             "unit": "TFLOP/s",
             "frac": flop_view["frac"],
             "traffic": traffic,
-            "flop_per_entry": flop_view["flop_per_entry"],
+            "flop_per_launch": flop_view["flop_per_launch"],
+            "ex2_peak_measured": ex2_peak,
         }
     roofline.update({
         "traffic_unit": "DRAM bytes per launch (ncu capture of the dominant instance; see its file)",
@@ -545,7 +806,12 @@ def run_ours(args):
         "grad_tflops": (prof["grad_flop"] / (prof["grad_ms"] / 1e3) / 1e12
                         if prof["grad_ms"] > 0 else None),
     })
-    grad_err = _kv_file(GRAD_ERROR_FILE)
+    extras = {}
+    if world == 1 and not args.no_extras:
+        extras["gradient_error"] = grad_error_leg(dev, stream, args.grad_reps)
+        extras["near_duplicates_kv"] = near_duplicates_leg(dev, stream, flush, args.c3_rows)
+        extras["uneven_batch"] = uneven_batch_leg(args, dev, stream, flush)
+        extras["small_2d_fp64_chain"] = small_2d_leg(dev, stream)
     line = {
         "metric": "SGLD steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -570,7 +836,10 @@ def run_ours(args):
                                                       for e in tab],
                              "cross_term": [e["cross_term"] for e in tab]}
                       for path, tab in tuned.items()} if tuned else None),
-        "gradient_error": ({k: grad_err[k] for k in grad_err} if grad_err else None),
+        "gradient_error": extras.get("gradient_error"),
+        "near_duplicates_kv": extras.get("near_duplicates_kv"),
+        "uneven_batch": extras.get("uneven_batch"),
+        "small_2d_fp64_chain": extras.get("small_2d_fp64_chain"),
         "mvp_rounds_per_step": rounds / K,
         "step_time_fit": fit,
         "at_equal_rounds": at_equal,
@@ -590,6 +859,9 @@ def run_ours(args):
         cb = oracle_sample(prob, work, args.cpu_seconds)
         line["cpu_baseline"] = {"value": cb["steps_per_s"], "unit": "steps/s",
                                 "cores": cb["cores"], "kind": "oracle", "sample": cb["sample"],
+                                "extrapolated": True,
+                                "extrapolation": "timed oracle rows scaled by n/m and by this "
+                                                 "run's measured work per step",
                                 "kv_entry_rhs_per_s": cb["kv_entry_rhs_per_s"]}
         line["work_per_step"] = {"mvp_entry_rhs_per_step": work["mvp_entry_rhs"],
                                  "grad_entries_per_step": work["grad_entries"],
@@ -601,20 +873,14 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
+def _batch_measure(args, dev, stream, flush, K, W, sampler=None, world=1, rank=0):
     """The 64-problem uneven workload: one batched SGLD step of all problems per graph launch
-    (persistent K V and gradient launches over all problems)."""
-    import numpy as np
+    (persistent K V and gradient launches over all problems).  Returns the measurement."""
     import torch
 
     from paper_1501_05427_gb300 import ulisse as u
     from paper_1501_05427_gb300 import workloads as w
-
-    world, rank, local = dist_setup(args, "nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
     probs = w.uneven_batch()
-    stream = torch.cuda.current_stream(dev)
     # the slowest of 576 columns decides a batched step's rounds; a column that has not
     # stopped after max_iter CG iterations is cut off (reported, not fatal)
     warm = not args.no_warm
@@ -622,16 +888,14 @@ def run_batch(args):
                                   eps=1e-8, max_iter=3000, seed=20150126 + 1000 * rank,
                                   probe_refresh=args.refresh, warm_start_probes=int(warm))
     allow = (u.ULISSE_ERR_MAXITER,)
-    cut = [0]
+    cut = 0
     Xs = [torch.from_numpy(p.X).to(dev) for p in probs]
     ys = [torch.from_numpy(p.y).to(dev) for p in probs]
     bc = u.BatchContext(Xs, ys, cfg, stream=stream)
     bc.set_graph(not args.no_graph)
-    K, W = args.steps, args.warmup
     psi = torch.tensor(np.concatenate([p.psi_true for p in probs]), dtype=torch.float64,
                        device=dev)
     eps = torch.full((max(K, W, 1),), EPS_T, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     psi_start = psi.clone()
     for k in range(W):
         psi.copy_(psi_start)
@@ -639,8 +903,8 @@ def run_batch(args):
     c0 = bc.counters()
     events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(K)]
-    sampler = ClockSampler(local)
-    sampler.start()
+    if sampler:
+        sampler.start()
     torch.cuda.synchronize(dev)
     rounds = []
     for k in range(K):
@@ -649,16 +913,17 @@ def run_batch(args):
         events[k][0].record(stream)
         st = bc.sgld_chain_status(psi, eps[k:k + 1], step0=W + k)
         events[k][1].record(stream)
-        cut[0] += int(st == u.ULISSE_ERR_MAXITER)
+        cut += int(st == u.ULISSE_ERR_MAXITER)
         rounds.append(bc.counters()[0])
     torch.cuda.synchronize(dev)
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     c1 = bc.counters()
     rounds = [b - a for a, b in zip([c0[0]] + rounds[:-1], rounds)]
     step_ms = [a.elapsed_time(b) for a, b in events]
     total_ms = sum(step_ms)
     n_sum = sum(p.n for p in probs)
-    line = {
+    bc.close()
+    return {
         "metric": "SGLD steps/s", "value": world * K * len(probs) / (total_ms / 1000.0),
         "unit": "problem-steps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -674,12 +939,23 @@ def run_batch(args):
                           "unit": "entry·RHS/s (whole step: K V rounds and the gradient sweep)"},
         "mvp_rounds_per_step": (c1[0] - c0[0]) / K,
         "rounds_per_step": rounds,
-        "steps_with_a_column_cut_at_max_iter": cut[0],
+        "steps_with_a_column_cut_at_max_iter": cut,
         "gpu_launches": int(c1[2] - c0[2]),
         "clocks": clocks,
         "step_ms": step_ms,
     }
-    bc.close()
+
+
+def run_batch(args):
+    """--workload uneven_batch: the batched line on its own."""
+    import torch
+    world, rank, local = dist_setup(args, "nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    line = _batch_measure(args, dev, stream, flush, args.steps, args.warmup,
+                          sampler=ClockSampler(local), world=world, rank=rank)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

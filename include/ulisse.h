@@ -460,6 +460,22 @@ ulisse_status ulisse_autotune(ulisse_ctx *ctx, const double *psi, int max_cols, 
  */
 ulisse_status ulisse_selftest_wait_timeout(ulisse_ctx *ctx);
 
+/*
+ * Device calibration (the paper has no counterpart; used for roofline reports): the
+ * throughput of the base-2 exponential (ex2.approx.ftz.f32), the one operation every
+ * generated covariance entry needs on the CUDA cores when the tensor cores form the rest.
+ * Runs independent exponentials on every SM of the current device (all resident threads,
+ * 16 in flight per thread) on `stream` (NULL: the legacy default stream), `reps` timed
+ * launches of about a millisecond each with CUDA events, and reports the best.
+ *   reps       1..1000.
+ *   ex2_per_s  host, out: exponentials per second of the best launch.
+ *   best_ms    host, out (may be NULL): duration of that launch.
+ * Needs no context and allocates nothing.  Synchronises the stream.
+ * Errors: ULISSE_ERR_ARG (ex2_per_s NULL or reps out of range), ULISSE_ERR_CUDA.
+ */
+ulisse_status ulisse_measure_ex2_rate(void *stream, int reps, double *ex2_per_s,
+                                      double *best_ms);
+
 /* Message for the last failing call on ctx (or on creation if ctx is NULL). */
 const char *ulisse_last_error(const ulisse_ctx *ctx);
 

@@ -35,7 +35,7 @@ EXPORTED = [
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
     "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
-    "ulisse_selftest_wait_timeout",
+    "ulisse_selftest_wait_timeout", "ulisse_measure_ex2_rate",
 ]
 
 
@@ -120,6 +120,7 @@ def load():
     lib.ulisse_grad.argtypes = [P, P, U64, P, sp]
     lib.ulisse_dk_bilinear.argtypes = [P, P, P, P, I, P, P]
     lib.ulisse_selftest_wait_timeout.argtypes = [P]
+    lib.ulisse_measure_ex2_rate.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
     lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
     lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
     lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
@@ -557,6 +558,19 @@ def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
     if st != ULISSE_OK:
         raise UlisseError(st, "ulisse_kmv_noalloc rejected the call")
     return out[:, 0] if V.dim() == 1 else out
+
+
+def ulisse_measure_ex2_rate(stream=None, reps=5):
+    """Exponentials per second of the current device (best of `reps` timed launches) and
+    the duration of that launch in ms."""
+    import torch
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    st = load().ulisse_measure_ex2_rate(ctypes.c_void_p(stream.cuda_stream), int(reps),
+                                        ctypes.byref(rate), ctypes.byref(ms))
+    if st != ULISSE_OK:
+        raise UlisseError(st, "ulisse_measure_ex2_rate failed")
+    return rate.value, ms.value
 
 
 def ulisse_ws_init(ctx: Context, **kw):

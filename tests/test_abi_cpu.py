@@ -90,3 +90,10 @@ def test_package_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(ulisse, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         ulisse.load()
+
+
+def test_measure_ex2_rate_rejects_bad_arguments(lib):
+    from paper_1501_05427_gb300 import ulisse
+    r = ctypes.c_double()
+    assert lib.ulisse_measure_ex2_rate(None, 0, ctypes.byref(r), None) == ulisse.ULISSE_ERR_ARG
+    assert lib.ulisse_measure_ex2_rate(None, 5, None, None) == ulisse.ULISSE_ERR_ARG
