@@ -9,6 +9,9 @@ numpy, using ``numpy.linalg.cholesky`` / triangular solves as library steps.
 
 Parameter vector: psi = (log l_1..log l_d, log sigma^2, log lambda), p = d + 2.
 
+Preconditioned CG with J = K + delta I (Sec. 3) and ULISSE on its outer iteration is in
+``oracle/pcg.py`` (numpy on the dense K).
+
 Pinning status of each function (what other than itself checks it) is listed in
 ``tests/test_oracle_pins.py``; every function here is pinned.
 """

@@ -38,6 +38,13 @@ a wrong sign or index, a transposed operand, a wrong weight) fails at least one 
                         the loss at a hand-built exact fit is 0, the ridge term alone
   mlp.pooled_constant   the loss gradient in b3 vanishes there (W3 = 0), and any other
                         constant has a larger loss
+  pcg.pcg_record        Cholesky solution (exact and inexact inner solves); d_i^T K d_j = 0
+                        and e_i^T z_j = 0; delta -> 0 solves in one step, delta -> infinity
+                        gives the C oracle's plain CG iterates; flexible beta = standard beta
+                        with exact inner solves
+  pcg.inner_cg          the stopping rule ||r|| <= tau ||e|| at the returned count, not before
+  pcg.ulisse_pcg_solve  reconstruction from the outer trajectory; E over the exact law of J is
+                        the Cholesky solution
 """
 import math
 import os
@@ -731,3 +738,116 @@ def test_mlp_forward_hand_evaluated():
     h2 = np.tanh(np.array([t5 + ln2 - 0.6, t7 + ln3 - 0.8]))
     assert np.allclose(C2[0], [2 * h2[0] - h2[1] + 0.25, 0.5 * h2[0] + h2[1] - 1.0],
                        rtol=0, atol=1e-14)
+
+
+# ----------------------------------------------------------------------------------------
+# Preconditioned CG, J = K + delta I (oracle/pcg.py; Sec. 3 "Preconditioned CG", Sec. 4)
+# ----------------------------------------------------------------------------------------
+def _pcg_problem(n=60, seed=21, noise=0.05):
+    X = _rand_X(n, 2, seed)
+    psi = np.log([0.25, 0.35, 1.0, noise])
+    b = np.random.default_rng(seed).standard_normal(n)
+    return X, psi, b
+
+
+def test_pcg_converges_to_cholesky(orc):
+    """Exact and inexact inner solves both reach the Cholesky solution (Sec. 3's error)."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem()
+    exact = orc.exact_solve(X, psi, b)
+    for kw in (dict(exact_inner=True), dict(tau=1e-3, inner_max=200), dict(tau=1e-1, inner_max=30)):
+        tr = pcg.pcg_record(X, psi, b, delta=0.3, eps=1e-10, **kw)
+        assert np.linalg.norm(tr["S"][-1] - exact) < 1e-7 * np.linalg.norm(exact), kw
+
+
+def test_pcg_invariants_with_exact_inner_solves(orc):
+    """With a fixed preconditioner the directions are K-conjugate and the residuals are
+    J^{-1}-orthogonal: d_i^T K d_j = 0 and e_i^T z_j = 0 for i != j (Golub & Van Loan)."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem(n=40)
+    K = orc.cov_matrix(X, psi)
+    tr = pcg.pcg_record(X, psi, b, delta=0.5, eps=1e-11, exact_inner=True, max_iter=8)
+    D, E, Z = tr["D"], tr["E"], tr["Z"]
+    m = min(len(D), 6)
+    G = D[:m] @ K @ D[:m].T
+    off = G - np.diag(np.diag(G))
+    assert np.max(np.abs(off)) < 1e-8 * np.max(np.abs(np.diag(G)))
+    H = E[:m] @ Z[:m].T
+    offh = H - np.diag(np.diag(H))
+    assert np.max(np.abs(offh)) < 1e-8 * np.max(np.abs(np.diag(H)))
+
+
+def test_pcg_limits(orc):
+    """delta -> 0 with exact inner solves: J = K and one outer iteration gives K^{-1} b.
+    delta -> infinity: J^{-1} -> I / delta, and PCG with a multiple of the identity is plain
+    CG -- the outer iterates equal the C oracle's Algorithm 1 (cg_record)."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem(n=50)
+    exact = orc.exact_solve(X, psi, b)
+    tr = pcg.pcg_record(X, psi, b, delta=0.0, eps=1e-9, exact_inner=True, max_iter=3)
+    assert np.linalg.norm(tr["S"][1] - exact) < 1e-9 * np.linalg.norm(exact)
+    tr = pcg.pcg_record(X, psi, b, delta=1e12, eps=1e-12, exact_inner=True, max_iter=8)
+    ref = orc.cg_record(X, psi, b, eps=1e-12, max_iter=8)
+    for i in range(1, 9):
+        assert np.linalg.norm(tr["S"][i] - ref["S"][i]) < 1e-7 * np.linalg.norm(ref["S"][i]), i
+
+
+def test_pcg_flexible_beta_equals_standard_with_exact_solves(orc):
+    """With exact inner solves e_{i+1}^T z_i = 0, so the flexible beta equals
+    e_{i+1}^T z_{i+1} / e_i^T z_i."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem(n=45)
+    tr = pcg.pcg_record(X, psi, b, delta=0.2, eps=1e-11, exact_inner=True, max_iter=6)
+    E, Z = tr["E"], tr["Z"]
+    for i in range(len(Z) - 1):
+        std = float(E[i + 1] @ Z[i + 1]) / float(E[i] @ Z[i])
+        assert abs(tr["beta"][i] - std) < 1e-9 * max(1.0, abs(std)), i
+
+
+def test_pcg_inner_cg_stopping_rule(orc):
+    """The inner CG stops at the first iteration with ||r|| <= tau ||e||: at that count the
+    residual of J z = e is below the threshold, one iteration earlier it is not."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem(n=50)
+    Jm = orc.cov_matrix(X, psi) + 0.2 * np.eye(50)
+    for tau in (1e-1, 1e-2, 1e-4):
+        x, k = pcg.inner_cg(Jm, b, tau, 500)
+        assert np.linalg.norm(b - Jm @ x) <= tau * np.linalg.norm(b) * (1 + 1e-9)
+        if k > 1:
+            x1, _ = pcg.inner_cg(Jm, b, tau, k - 1)
+            assert np.linalg.norm(b - Jm @ x1) > tau * np.linalg.norm(b) * (1 - 1e-9)
+
+
+def test_ulisse_on_pcg_expectation_by_enumeration(orc):
+    """Sec. 4 applies to the outer PCG iteration: the estimates are the reconstruction from
+    the outer trajectory, and E over the exact law of J is the converged solution, which is
+    the Cholesky solution."""
+    from oracle import pcg
+    X, psi, b = _pcg_problem(n=40, noise=0.2)
+    q, beta = 0.3, 1.0
+    tr = pcg.pcg_record(X, psi, b, delta=0.4, tau=1e-3, inner_max=200, eps=1e-11)
+    S, T = tr["S"], tr["T"]
+    norms = np.linalg.norm(tr["E"], axis=1)
+    l = next(i for i in range(1, T + 1) if norms[i] < q * math.sqrt(40))
+    assert T - l <= 30
+    mean = np.zeros(40)
+    for J in range(0, T - l + 1):
+        pJ = math.exp(-beta * J * (J + 1) / 2) - (math.exp(-beta * (J + 1) * (J + 2) / 2)
+                                                  if J < T - l else 0.0)
+        est = S[l].copy()
+        for j in range(1, J + 1):
+            est += pcg.weight(j, beta) * (S[l + j] - S[l + j - 1])
+        mean += pJ * est
+    exact = orc.exact_solve(X, psi, b)
+    assert np.linalg.norm(mean - exact) < 1e-7 * np.linalg.norm(exact)
+    # the solver's estimates are those reconstructions with the drawn J
+    Bm = np.repeat(b[:, None], 16, axis=1)
+    Sest, st, _ = pcg.ulisse_pcg_solve(X, psi, Bm, delta=0.4, tau=1e-3, inner_max=200, q=q,
+                                       beta=beta, eps=1e-11, seed=9, step=2)
+    for c in range(16):
+        J = int(st[c, 3])
+        ref = S[l].copy()
+        for j in range(1, min(J, T - l) + 1):
+            ref += pcg.weight(j, beta) * (S[l + j] - S[l + j - 1])
+        assert st[c, 0] == l and st[c, 1] == min(l + J, T)
+        assert np.linalg.norm(Sest[:, c] - ref) < 1e-12 * np.linalg.norm(ref)
