@@ -18,8 +18,8 @@ exponential unit's rate measured on the device in the same run.
 At N = 1 the same line carries the other configurations as keys: the gradient error of the
 paths (Sec. 5's measure, dense FP64 Cholesky reference on the device), the near-duplicate
 K V at full size (n = 200,000, d = 16, 64 RHS) with its error against oracle rows, the
-64-problem uneven batch, and the 2-D FP64 100-step chain beside the oracle's full chain
-(--no-extras skips them).
+64-problem uneven batch, the 2-D FP64 100-step chain beside the oracle's full chain, and
+preconditioned CG (Sec. 3) against plain CG with cold solves (--no-extras skips them).
 
 --impl reference times the FP64 CPU oracle on the host cores instead (a bounded sample of
 the same workload, scaled to SGLD steps/s).  With N > 1 (torchrun) every rank runs an
@@ -629,6 +629,46 @@ def small_2d_leg(dev, stream, n_steps=100):
     return out
 
 
+def pcg_leg(dev, stream, flush, X, y, psi0, steps=6, warm=2):
+    """Sec. 3's preconditioned CG (J = K + delta I, inner CG to ||r|| <= 0.1 ||e||) with ULISSE
+    on the outer iteration, against plain CG, both with cold solves (probes redrawn every
+    step: every step is a probe-epoch start) on the tensor-core path, from the host loop:
+    K V rounds per step (outer and inner) and steps/s, for a few delta (the paper tunes
+    delta for the fewest iterations)."""
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    out = {"solves": "cold (zero start), probes redrawn every step", "inner_tol": 0.1,
+           "inner_max": 50, "step_form": "host loop"}
+    legs = [("cg", 0.0)] + [("pcg_delta_%g" % dl, dl) for dl in (0.1, 0.5, 2.0)]
+    for name, dl in legs:
+        cfg = u.ulisse_config_default(n_probes=N_PROBES, precision=u.PREC_MIXED, q=1.0, beta=1.0,
+                                      max_iter=1000, seed=20150123, pcg_delta=dl,
+                                      pcg_inner_tol=0.1, pcg_inner_max=50)
+        with u.Context(X, y, cfg, stream=stream) as ctx:
+            ctx.set_graph(False)
+            for k in range(warm):
+                ctx.sgld_step(psi0, EPS_T, step=10_000 + k, allow=(u.ULISSE_ERR_MAXITER,))
+            r0 = ctx.counters()[0]
+            ms = []
+            for k in range(steps):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                a.record(stream)
+                ctx.sgld_step(psi0, EPS_T, step=k, allow=(u.ULISSE_ERR_MAXITER,))
+                b.record(stream)
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+            out[name] = {"steps_per_s": 1000.0 * steps / sum(ms),
+                         "mvp_rounds_per_step": (ctx.counters()[0] - r0) / steps}
+    best = min((k for k in out if k.startswith("pcg_")), key=lambda k: out[k]["mvp_rounds_per_step"])
+    out["fewest_rounds"] = best
+    out["rounds_pcg_over_cg"] = out[best]["mvp_rounds_per_step"] / out["cg"]["mvp_rounds_per_step"]
+    return out
+
+
 def uneven_batch_leg(args, dev, stream, flush, K=5, W=2):
     """The 64-problem uneven batch, one graph launch per batched step (see run_batch)."""
     return _batch_measure(args, dev, stream, flush, K, W, sampler=None)
@@ -812,6 +852,7 @@ def run_ours(args):
         extras["near_duplicates_kv"] = near_duplicates_leg(dev, stream, flush, args.c3_rows)
         extras["uneven_batch"] = uneven_batch_leg(args, dev, stream, flush)
         extras["small_2d_fp64_chain"] = small_2d_leg(dev, stream)
+        extras["pcg"] = pcg_leg(dev, stream, flush, X, y, prob.psi_true)
     line = {
         "metric": "SGLD steps/s", "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": K, "warmup": W, "ms_per_step": total_ms / K, "higher_is_better": True,
@@ -840,6 +881,7 @@ def run_ours(args):
         "near_duplicates_kv": extras.get("near_duplicates_kv"),
         "uneven_batch": extras.get("uneven_batch"),
         "small_2d_fp64_chain": extras.get("small_2d_fp64_chain"),
+        "pcg": extras.get("pcg"),
         "mvp_rounds_per_step": rounds / K,
         "step_time_fit": fit,
         "at_equal_rounds": at_equal,

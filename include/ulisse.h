@@ -93,10 +93,20 @@ typedef struct {
                                 TF32 high part and the remainder), 0 = the default (2) or the
                                 autotuner's choice.  The two differ in the last bits of each
                                 kernel value (relative 1e-6 to 1e-5). */
+    double pcg_delta;        /* 0: the solves run CG (Algorithm 1).  > 0: preconditioned CG
+                                with J = K + pcg_delta I (Sec. 3, "Preconditioned CG"), every
+                                iteration solving J z = e by an inner CG on the same K V
+                                products (same precision); ULISSE truncates the outer
+                                iteration (Sec. 4).  Solves then start from zero
+                                (warm_start_probes = 0, no S0, no learned warm start) and a
+                                step runs from the host loop. */
+    double pcg_inner_tol;    /* inner CG stops at ||r|| <= pcg_inner_tol ||e||, 0 < tol < 1 */
+    int pcg_inner_max;       /* ... or after this many inner iterations (>= 1) */
 } ulisse_config;
 
 /* Fill *cfg with the paper's settings: FP32, 4 Rademacher probes redrawn every step,
- * q = 1, beta = 1, eps = 1e-8, max_iter = 1000, seed 0, tuned K V tile shape. */
+ * q = 1, beta = 1, eps = 1e-8, max_iter = 1000, seed 0, tuned K V tile shape, plain CG
+ * (pcg_delta = 0; pcg_inner_tol = 1e-2, pcg_inner_max = 100 when enabled). */
 void ulisse_config_default(ulisse_config *cfg);
 
 /*

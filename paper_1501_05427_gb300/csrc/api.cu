@@ -9,6 +9,7 @@
 
 #include "../../include/ulisse.h"
 #include "solver_kernels.cuh"
+#include "pcg_kernels.cuh"
 #include "warm_start.cuh"
 #include "batch.cuh"
 
@@ -135,6 +136,12 @@ struct ulisse_ctx {
   double* b_psi = nullptr;         // device: packed parameters of all problems
   int b_np = 0;                    // packed parameter count
   int b_maxch = 1;                 // largest chunk count of the batched CG launches
+
+  // preconditioned CG (cfg.pcg_delta > 0): Z, X, Rr, P, KP (pcg_cap columns each)
+  void* pcg_buf = nullptr;
+  int pcg_cap = 0;
+  PcgAux* pcg_aux = nullptr;
+  int* pcg_live = nullptr;
 
   // event timing of the O(n^2) kernels (ulisse_profile_enable)
   bool prof = false;
@@ -610,9 +617,137 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned lo
   return ULISSE_OK;
 }
 
+// Preconditioned CG (cfg.pcg_delta > 0) with ULISSE on the outer iteration, columns 0..R-1
+// of B, zero start; see pcg_kernels.cuh.  The host learns which columns are live after every
+// outer iteration and every inner one (one small read each, as solve_core does) and launches
+// K V on those columns only; every K V product, outer or inner, counts as a round.
+template <typename T>
+static ulisse_status pcg_core(ulisse_ctx* ctx, int R, unsigned long long step) {
+  if (ctx->pcg_cap < ctx->cap) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx->pcg_buf);
+    dev_free(reinterpret_cast<void*&>(ctx->pcg_aux));
+    dev_free(reinterpret_cast<void*&>(ctx->pcg_live));
+    CKS(dev_alloc(ctx, &ctx->pcg_buf, (size_t)ctx->ldn * ctx->esz * ctx->cap * 5));
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->pcg_aux), sizeof(PcgAux) * ctx->cap));
+    CKS(dev_alloc(ctx, reinterpret_cast<void**>(&ctx->pcg_live), sizeof(int) * ctx->cap));
+    // the padding rows of every vector stay zero (the K V kernels read whole tiles)
+    CK(cudaMemsetAsync(ctx->pcg_buf, 0, (size_t)ctx->ldn * ctx->esz * ctx->cap * 5, ctx->stream));
+    ctx->pcg_cap = ctx->cap;
+  }
+  const size_t blk = (size_t)ctx->ldn * ctx->cap;   // elements per buffer
+  T* base = (T*)ctx->pcg_buf;
+  PcgArgs<T> a;
+  a.S = (T*)ctx->S;
+  a.E = (T*)ctx->E;
+  a.D = (T*)ctx->D;
+  a.KD = (const T*)ctx->KD;
+  a.Z = base;
+  a.X = base + blk;
+  a.Rr = base + 2 * blk;
+  a.P = base + 3 * blk;
+  a.KP = base + 4 * blk;
+  a.B = (const T*)ctx->B;
+  a.SE = (T*)ctx->SE;
+  a.n = ctx->n;
+  a.ld = ctx->ldn;
+  a.st = ctx->st;
+  a.aux = ctx->pcg_aux;
+  a.live = ctx->pcg_live;
+  a.alpha_thr = ctx->cfg.q * std::sqrt((double)ctx->n);
+  a.eps = ctx->cfg.eps;
+  a.beta = ctx->cfg.beta;
+  a.delta = ctx->cfg.pcg_delta;
+  a.tau = ctx->cfg.pcg_inner_tol;
+  a.max_iter = ctx->cfg.max_iter;
+  a.inner_max = ctx->cfg.pcg_inner_max;
+  a.seed = ctx->cfg.seed;
+  a.step = step;
+  a.status = ctx->status_dev;
+
+  std::vector<int> cols;
+  auto upload = [&](const std::vector<int>& v) -> ulisse_status {
+    CK(cudaMemcpyAsync(ctx->pcg_live, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+    return ULISSE_OK;
+  };
+  // columns whose outer iteration is still running
+  std::vector<ColState> hst(R);
+  auto outer_live = [&](std::vector<int>& out) -> ulisse_status {
+    CK(cudaMemcpyAsync(hst.data(), ctx->st, sizeof(ColState) * R, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    prof_drain(ctx);
+    out.clear();
+    for (int c = 0; c < R; ++c)
+      if (hst[c].phase != kDone) out.push_back(c);
+    return ULISSE_OK;
+  };
+  std::vector<PcgAux> hax(R);
+  // z = J^{-1} e for the listed columns (inner CG), then the new directions
+  auto precondition = [&](const std::vector<int>& L) -> ulisse_status {
+    CKS(upload(L));
+    pcg_inner_init_kernel<T><<<(unsigned)L.size(), kPcgNT, 0, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    std::vector<int> in = L;
+    for (int k = 0; k < ctx->cfg.pcg_inner_max && !in.empty(); ++k) {
+      CKS(upload(in));
+      CKS(run_kmv(ctx, a.P, ctx->pcg_live, (int)in.size(), (void*)a.KP, ctx->pcg_live, kModeK,
+                  -1));
+      ctx->mvp_rounds += 1;
+      pcg_inner_step_kernel<T><<<(unsigned)in.size(), kPcgNT, 0, ctx->stream>>>(a);
+      CK(cudaGetLastError());
+      ctx->launches++;
+      CK(cudaMemcpyAsync(hax.data(), ctx->pcg_aux, sizeof(PcgAux) * R, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      prof_drain(ctx);
+      std::vector<int> next;
+      for (int c : in)
+        if (!hax[c].inner_done) next.push_back(c);
+      in.swap(next);
+    }
+    CKS(upload(L));
+    pcg_dir_kernel<T><<<(unsigned)L.size(), kPcgNT, 0, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    return ULISSE_OK;
+  };
+
+  for (int c = 0; c < R; ++c) cols.push_back(c);
+  CKS(upload(cols));
+  pcg_init_kernel<T><<<R, kPcgNT, 0, ctx->stream>>>(a);
+  CK(cudaGetLastError());
+  ctx->launches++;
+  CKS(outer_live(cols));
+  if (!cols.empty()) CKS(precondition(cols));
+  for (int it = 0; it < ctx->cfg.max_iter; ++it) {
+    CKS(outer_live(cols));
+    if (cols.empty()) break;
+    CKS(upload(cols));
+    CKS(run_kmv(ctx, ctx->D, ctx->pcg_live, (int)cols.size(), ctx->KD, ctx->pcg_live, kModeK,
+                -1));
+    ctx->mvp_rounds += 1;
+    pcg_step_kernel<T><<<(unsigned)cols.size(), kPcgNT, 0, ctx->stream>>>(a);
+    CK(cudaGetLastError());
+    ctx->launches++;
+    CKS(outer_live(cols));
+    if (cols.empty()) break;
+    CKS(precondition(cols));
+  }
+  return ULISSE_OK;
+}
+
 static ulisse_status solve_dispatch(ulisse_ctx* ctx, int R, int s0_cols,
                                     unsigned long long step, bool warm = false,
                                     bool y_learned = false) {
+  if (ctx->cfg.pcg_delta > 0.0) {
+    if (s0_cols > 0 || warm || y_learned)
+      return fail(ctx, ULISSE_ERR_ARG, "preconditioned CG solves start from zero (no S0, "
+                                       "no warm-started solves, no learned warm start)");
+    return ctx->f64 ? pcg_core<double>(ctx, R, step) : pcg_core<float>(ctx, R, step);
+  }
   return ctx->f64 ? solve_core<double>(ctx, R, s0_cols, step, warm, y_learned)
                   : solve_core<float>(ctx, R, s0_cols, step, warm, y_learned);
 }
@@ -785,6 +920,12 @@ static ulisse_status check_cfg(const ulisse_config* c) {
   if (c->kmv_rows_per_thread != 0 && c->kmv_rows_per_thread != 2 && c->kmv_rows_per_thread != 4)
     return ULISSE_ERR_ARG;
   if (c->tc_cross_term < 0 || c->tc_cross_term > 2) return ULISSE_ERR_ARG;
+  if (!(c->pcg_delta >= 0.0) || !std::isfinite(c->pcg_delta)) return ULISSE_ERR_ARG;
+  if (c->pcg_delta > 0.0) {
+    if (!(c->pcg_inner_tol > 0.0 && c->pcg_inner_tol < 1.0) || c->pcg_inner_max < 1)
+      return ULISSE_ERR_ARG;
+    if (c->warm_start_probes != 0) return ULISSE_ERR_ARG;   // PCG solves start from zero
+  }
   return ULISSE_OK;
 }
 
@@ -907,6 +1048,9 @@ void ulisse_config_default(ulisse_config* cfg) {
   cfg->seed = 0;
   cfg->kmv_rows_per_thread = 0;
   cfg->tc_cross_term = 0;
+  cfg->pcg_delta = 0.0;
+  cfg->pcg_inner_tol = 1e-2;
+  cfg->pcg_inner_max = 100;
 }
 
 ulisse_status ulisse_create(ulisse_ctx** out, const float* X, const float* y, long long n, int d,
@@ -1388,7 +1532,7 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
 }
 
 static bool graph_usable(const ulisse_ctx* ctx) {
-  return ctx->graph_enabled && !ctx->prof && !ctx->ws_record;
+  return ctx->graph_enabled && !ctx->prof && !ctx->ws_record && !(ctx->cfg.pcg_delta > 0.0);
 }
 
 static ulisse_status graph_alloc(ulisse_ctx* ctx) {
@@ -2558,7 +2702,8 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->part2), reinterpret_cast<void**>(&ctx->bneg),
                    &ctx->Vt_hi, &ctx->Vt_lo, &ctx->Gt_hi, &ctx->Gt_lo,
                    reinterpret_cast<void**>(&ctx->Xt_hi), reinterpret_cast<void**>(&ctx->Xt_lo),
-                   reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa})
+                   reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa, &ctx->pcg_buf,
+                   reinterpret_cast<void**>(&ctx->pcg_aux), reinterpret_cast<void**>(&ctx->pcg_live)})
     dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,
                    reinterpret_cast<void**>(&ctx->params), reinterpret_cast<void**>(&ctx->psi_dev),

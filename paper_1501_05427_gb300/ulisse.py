@@ -53,6 +53,9 @@ class ulisse_config(ctypes.Structure):
         ("seed", ctypes.c_ulonglong),
         ("kmv_rows_per_thread", ctypes.c_int),
         ("tc_cross_term", ctypes.c_int),
+        ("pcg_delta", ctypes.c_double),
+        ("pcg_inner_tol", ctypes.c_double),
+        ("pcg_inner_max", ctypes.c_int),
     ]
 
 

@@ -45,11 +45,15 @@ def test_config_default(lib):
     cfg = ulisse.ulisse_config_default()
     assert cfg.q == 1.0 and cfg.beta == 1.0 and cfg.eps == 1e-8
     assert cfg.n_probes == 4 and cfg.probe_refresh == 1 and cfg.precision == 0
+    # the fields after the original ones sit where the C struct has them
+    assert cfg.pcg_delta == 0.0 and cfg.pcg_inner_tol == 1e-2 and cfg.pcg_inner_max == 100
 
 
 @pytest.mark.parametrize("n,d,bad_cfg", [(0, 2, None), (10, 0, None), (10, 17, None),
                                          (10, 2, "n_probes"), (10, 2, "beta"),
-                                         (10, 2, "q"), (10, 2, "refresh"), (10, 2, "cross")])
+                                         (10, 2, "q"), (10, 2, "refresh"), (10, 2, "cross"),
+                                         (10, 2, "pcg_delta"), (10, 2, "pcg_tol"),
+                                         (10, 2, "pcg_max"), (10, 2, "pcg_warm")])
 def test_create_rejects_bad_arguments(lib, n, d, bad_cfg):
     from paper_1501_05427_gb300 import ulisse
     cfg = ulisse.ulisse_config_default()
@@ -63,6 +67,14 @@ def test_create_rejects_bad_arguments(lib, n, d, bad_cfg):
         cfg.probe_refresh = 0
     elif bad_cfg == "cross":
         cfg.tc_cross_term = 3
+    elif bad_cfg == "pcg_delta":
+        cfg.pcg_delta = -0.5
+    elif bad_cfg == "pcg_tol":
+        cfg.pcg_delta, cfg.pcg_inner_tol = 0.1, 1.0
+    elif bad_cfg == "pcg_max":
+        cfg.pcg_delta, cfg.pcg_inner_max = 0.1, 0
+    elif bad_cfg == "pcg_warm":
+        cfg.pcg_delta, cfg.warm_start_probes = 0.1, 1
     X = np.zeros((max(n, 1), max(d, 1)), np.float32)
     y = np.zeros(max(n, 1), np.float32)
     h = ctypes.c_void_p()
