@@ -12,22 +12,15 @@
 //      over C's own columns (tcgen05.st);
 //   3. U_I += K_IJ V_J on the tensor cores with V split into BF16 high + low parts (three
 //      products), FP32 accumulation in tensor memory, as in the FP32-pipe variant.
-// A_I stays in tensor memory for the CTA's whole j range: the first epilogue set writes its
-// TF32 high parts and remainders there once, and the C products read their A operand from
-// tensor memory.  (An MMA whose A operand sits in shared memory re-reads it for every
-// instruction: 4 KB per 128 x 8 TF32 step, which at 128 bytes per clock bounds these small
-// MMAs by the shared-memory bandwidth.)  The TF32 image of B (high and low parts, K-major
-// canonical, 32-point tiles back to back) is written once per parameter value by
-// pack_x_tf32_kernel.  Roles: warp 0 streams the B_J image and V_J into a ring of three to
-// eight stages with bulk copies; one thread of warp 1 issues the MMAs, with descriptors
-// formed once (one thread issues about one MMA per 45 cycles, so its own instructions pace
-// the pipeline); eight epilogue warps make the kernel values, in two sets of four (one per
-// tensor-memory lane quadrant) that take alternate tiles whole, so that each wait and
-// hand-off covers 32 entries per thread.  Two or three C/K buffers (128 tensor-memory
-// columns, four CTAs per SM), or three with 256 columns and two CTAs per SM where the
-// accumulator is wide; a buffer is refilled only after the MMAs that read it have completed.
-// Every wait is bounded.  The split j range, the fixed-order fix-up of the partial sums and
-// the FP32 diagonal term lambda V are those of the FP32-pipe variant.
+// The TF32 images of A and B (high and low parts, K-major canonical, 32-point tiles back to
+// back so that four tiles form the 128-row A operand) are written once per parameter value by
+// pack_x_tf32_kernel.  Roles: warp 0 streams the A image once, then the B_J image and V_J
+// into a 3- or 4-stage ring with bulk copies; one thread of warp 1 issues the MMAs; eight
+// epilogue warps make the kernel values, in two sets of four (one per tensor-memory lane
+// quadrant) that take alternate tiles whole, so that each wait and hand-off covers 32
+// entries per thread.  Three C/K buffers (two when the accumulator takes 64 columns); a buffer
+// is refilled only after the MMAs that read it have completed.  Every wait is bounded.  The split j range, the fixed-order fix-up of the
+// partial sums and the FP32 diagonal term lambda V are those of the FP32-pipe variant.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,37 +34,45 @@ namespace ulisse {
 constexpr int kT2BN = 32;
 constexpr int kT2BM = 128;
 constexpr int kT2Threads = 320;    // warp 0 producer, warp 1 MMA issuer, warps 2-9 epilogue
+constexpr uint32_t kT2Cols = 128;  // tensor-memory columns per CTA
 
-// The augmented rows B_j = [2 c1 x^_j, b_j, 0...] for j in [0, rows) as TF32 high part and
-// remainder, K8 columns, in 32-row K-major canonical tiles; rows >= n are zero.  b_j =
-// -c1 |x^_j|^2 is read from the row norms of launch_prescale_tc.  (The A rows [x^_i, 1] are
-// built by the K V kernel itself, in tensor memory.)
+// The augmented rows A_j = [x^_j, 1, 0...] and B_j = [2 c1 x^_j, b_j, 0...] for j in [0, rows)
+// as TF32 high part and remainder, K8 columns, in 32-row K-major canonical tiles; rows >= n
+// are zero.  b_j = -c1 |x^_j|^2 is read from the row norms of launch_prescale_tc.
 __global__ void pack_x_tf32_kernel(const float* __restrict__ xhat, const float* __restrict__ bneg,
                                    const DevParams* __restrict__ params, int DP, int K8,
-                                   long long n, long long rows, float* __restrict__ Bhi,
+                                   long long n, long long rows, float* __restrict__ Ahi,
+                                   float* __restrict__ Alo, float* __restrict__ Bhi,
                                    float* __restrict__ Blo) {
   const float two_c1 = 2.f * params->c1f;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < rows * K8;
        idx += (long long)gridDim.x * blockDim.x) {
     const long long j = idx / K8;
     const int k = (int)(idx - j * K8);
-    float vb = 0.f;
+    float va = 0.f, vb = 0.f;
     if (j < n) {
-      if (k < DP) vb = two_c1 * xhat[j * DP + k];
-      else if (k == DP) vb = bneg[j];
+      if (k < DP) {
+        va = xhat[j * DP + k];
+        vb = two_c1 * va;
+      } else if (k == DP) {
+        va = 1.f;
+        vb = bneg[j];
+      }
     }
     const long long t = j / kT2BN;
     const int jj = (int)(j - t * kT2BN);
     const long long off = t * kT2BN * K8 + tc::canon_offset(jj, k, 4, K8 / 4) / 4;
-    const float hb = tc::tf32_round(vb);
+    const float ha = tc::tf32_round(va), hb = tc::tf32_round(vb);
+    Ahi[off] = ha;
+    Alo[off] = va - ha;
     Bhi[off] = hb;
     Blo[off] = vb - hb;
   }
 }
 
 struct Tc2DevArgs {
-  const float* xhat;     // prescaled inputs, ldn x DP row-major (the A rows are built from it)
-  int DP;
+  const float* A_hi;     // TF32 image of the augmented A rows (high part)
+  const float* A_lo;     // remainder
   const float* B_hi;     // TF32 image of the augmented B rows
   const float* B_lo;
   const float* bneg;     // -c1 |x^|^2
@@ -94,40 +95,24 @@ struct Tc2DevArgs {
 
 template <int K8, int N>
 struct Tc2Shape {
-  // tensor memory: the TF32 image of the CTA's augmented rows A_I (high part in columns
-  // [0, K8), remainder in [K8, 2 K8)), then NB C/K buffers of 32 columns, then the
-  // accumulator U (N columns).  128 columns and four CTAs per SM while two buffers fit, else
-  // 256 columns and two CTAs per SM.
-  static constexpr uint32_t COL_A = 0;
-  static constexpr uint32_t A_COLS = 2 * K8;
-  static constexpr uint32_t COLS = (A_COLS + 2 * 32 + N <= 128) ? 128u : 256u;
-  static constexpr int CTAS = COLS == 128 ? 4 : 2;
-  static constexpr int NB_FIT = (int)((COLS - A_COLS - (uint32_t)N) / 32);
-  static constexpr int NB = NB_FIT < 3 ? NB_FIT : 3;
-  static constexpr uint32_t COL_C = A_COLS;
-  static constexpr uint32_t COL_U = COL_C + NB * 32;   // after the C/K buffers
+  static constexpr uint32_t A_BYTES = kT2BM * K8 * 4;   // one part of the A_I image
   static constexpr uint32_t XB_BYTES = kT2BN * K8 * 4;  // one part of the B_J image
   static constexpr uint32_t V_BYTES = N * kT2BN * 2;    // one part of the BF16 V_J tile
   static constexpr uint32_t STAGE_BYTES = 2 * XB_BYTES + 2 * V_BYTES;
-  // the stage ring: as deep as the CTA's share of shared memory allows (4 CTAs: ~54 KB each,
-  // 2 CTAs: ~110 KB each), three to eight stages
-  static constexpr uint32_t SMEM_CTA = CTAS == 4 ? 54 * 1024 : 110 * 1024;
-  static constexpr int ST_FIT = (int)((SMEM_CTA - 512) / STAGE_BYTES);
-  static constexpr int ST = ST_FIT < 3 ? 3 : (ST_FIT > 8 ? 8 : ST_FIT);
-  static constexpr uint32_t OFF_STAGES = 0;
+  // four stages while four CTAs still fit in shared memory (~54 KB each), else three
+  static constexpr int ST = (2 * A_BYTES + 4 * STAGE_BYTES <= 54 * 1024) ? 4 : 3;
+  static constexpr uint32_t OFF_STAGES = 2 * A_BYTES;
   static constexpr uint32_t OFF_BARS = OFF_STAGES + ST * STAGE_BYTES;
-  // full, empty per stage; a_full (the four warps that write A_I arrive); c_full per tile
-  // mod NCF; k_full, b_free per buffer; done.  The MMA issuer refills buffers in tile order
-  // and issues tile p's C only after tile p - NB's contraction, which waited for tile
-  // p - NB's K (and, in order, every earlier tile's); so with NCF a multiple of the two
-  // epilogue sets and NCF >= NB, each c_full barrier serves one set, and a phase completes
-  // only after that set has waited for the previous one.
-  static constexpr int NCF = 2 * ((NB + 1) / 2);
+  // C/K buffers of 32 columns: three while they fit beside the accumulator, else two
+  static constexpr int NB = (3 * 32 + N <= (int)kT2Cols) ? 3 : 2;
+  // full, empty per stage; a_full; c_full per tile mod 6 (so that each barrier serves one
+  // epilogue set and its phases are waited in order); k_full, b_free per buffer; done
+  static constexpr int NCF = 6;
   static constexpr int NBARS = 2 * ST + 1 + NCF + 2 * NB + 1;
   static constexpr uint32_t SMEM = OFF_BARS + NBARS * 8 + 64;
-  static_assert(NB >= 2, "at least two C/K buffers");
-  static_assert(COL_U + N <= COLS, "tensor memory layout exceeds the allocation");
-  static_assert(STAGE_BYTES % 16 == 0 && XB_BYTES % 16 == 0,
+  static constexpr uint32_t COL_U = NB * 32;   // after the C/K buffers
+  static_assert(COL_U + N <= kT2Cols, "tensor memory layout exceeds the allocation");
+  static_assert(STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 && XB_BYTES % 16 == 0,
                 "bulk copies and descriptors need 16-byte alignment");
 };
 
@@ -156,13 +141,14 @@ __device__ inline void t2_ld_cols(uint32_t taddr, float (&v)[NH]) {
 }
 
 template <int K8, int N>
-__global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
-    kmv_tc2_kernel(const Tc2DevArgs a) {
+__global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs a) {
   using S = Tc2Shape<K8, N>;
   constexpr int ST = S::ST;
   constexpr int NB = S::NB;
   constexpr int NH = N / 2;
   extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sAh = smem;
+  unsigned char* sAl = smem + S::A_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + S::OFF_BARS);
   uint64_t* full = bars;
   uint64_t* empty = bars + ST;
@@ -188,7 +174,7 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);   // the MMA commit: only the tensor cores read a stage
     }
-    mbar_init(a_full, 4);   // the four warps of epilogue set 0, once A_I is in tensor memory
+    mbar_init(a_full, 1);
     for (int c = 0; c < S::NCF; ++c) mbar_init(&c_full[c], 1);
     for (int b = 0; b < NB; ++b) {
       mbar_init(&k_full[b], 4);   // the four epilogue warps of the tile's set
@@ -198,7 +184,7 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
     fence_barrier_init();
     *s_fail = 0;
   }
-  if (warp == 1) tc::tmem_alloc(s_tmem, S::COLS);
+  if (warp == 1) tc::tmem_alloc(s_tmem, kT2Cols);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -206,8 +192,11 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
   int issued = 0;   // tiles whose copies the producer started (lane 0 of warp 0)
 
   if (warp == 0) {
-    // ---------------- producer: the B_J image and V_J of every tile into the ring ----------
+    // ---------------- producer: the x^_I image, then x^_J, b_J, V_J into the ring ----------
     if (lane == 0) {
+      mbar_arrive_expect_tx(a_full, 2 * S::A_BYTES);
+      bulk_g2s(sAh, a.A_hi + row0 * K8, S::A_BYTES, a_full);
+      bulk_g2s(sAl, a.A_lo + row0 * K8, S::A_BYTES, a_full);
       for (int lt = 0; lt < nt; ++lt) {
         const int s = lt % ST;
         if (lt >= ST && !mbar_wait_backoff(&empty[s], (uint32_t)(((lt / ST) - 1) & 1))) {
@@ -227,19 +216,13 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
       }
     }
   } else if (warp == 1) {
-    // ---------------- MMA issuer: C = A_I B_J^T, then U += K V ----------------
-    // One thread issues every MMA of the CTA.  A_I is read from tensor memory (an MMA whose
-    // A operand sits in shared memory re-reads 4 KB of it per instruction, which bounds small
-    // MMAs by the shared-memory bandwidth), B_J and V_J from the ring; the descriptors are
-    // formed once (a byte offset o within shared memory adds o / 16 to a descriptor) and the
-    // waits poll without sleeping.
+    // ---------------- MMA issuer: C = x^_I x^_J^T, then U += K V ----------------
     if (lane == 0) {
       constexpr uint32_t idesc_c = tc::instr_desc(2, kT2BM, kT2BN);   // TF32
       constexpr uint32_t idesc_u = tc::instr_desc(1, kT2BM, N);       // BF16
       constexpr uint32_t sbo_x = (K8 / 4) * 128;
-      constexpr uint64_t kStage = S::STAGE_BYTES >> 4, kXB = S::XB_BYTES >> 4;
-      constexpr uint64_t kVB = S::V_BYTES >> 4;
-      const uint32_t tAh = tbase + S::COL_A, tAl = tAh + K8;
+      const uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl);
+      const uint64_t dAh = tc::smem_desc(aH, 128, sbo_x), dAl = tc::smem_desc(aL, 128, sbo_x);
       const uint64_t dB0 = tc::smem_desc(smem_u32(stage(0)), 128, sbo_x);
       const uint64_t dV0 = tc::smem_desc(smem_u32(stage(0)) + 2 * S::XB_BYTES, 128, 512);
       bool ok = mbar_wait_spin(a_full, 0);
@@ -247,15 +230,15 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
         const int s = p % ST, b = p % NB;
         if (!mbar_wait_spin(&full[s], (uint32_t)((p / ST) & 1))) return false;
         tc::fence_after();
-        const uint64_t dBh = dB0 + (uint64_t)s * kStage, dBl = dBh + kXB;
-        const uint32_t dC = tbase + S::COL_C + (uint32_t)(b * 32);
+        const uint64_t dBh = dB0 + (uint64_t)s * (S::STAGE_BYTES >> 4), dBl = dBh + (S::XB_BYTES >> 4);
+        const uint32_t dC = tbase + (uint32_t)(b * 32);
 #pragma unroll
         for (int term = 0; term < 3; ++term) {
-          const uint32_t A = term == 2 ? tAl : tAh;
+          const uint64_t A = term == 2 ? dAl : dAh;
           const uint64_t B = term == 1 ? dBl : dBh;
 #pragma unroll
-          for (int ks = 0; ks < K8 / 8; ++ks)   // 8 TF32 elements = 8 columns per k-step
-            tc::mma_tf32_ts(dC, A + 8u * ks, B + 16u * ks, idesc_c, (term | ks) != 0);
+          for (int ks = 0; ks < K8 / 8; ++ks)
+            tc::mma_tf32(dC, A + 16u * ks, B + 16u * ks, idesc_c, (term | ks) != 0);
         }
         tc::commit(&c_full[p % S::NCF]);
         return true;
@@ -267,16 +250,15 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
         const int s = p % ST, b = p % NB;
         if (!mbar_wait_spin(&k_full[b], (uint32_t)((p / NB) & 1))) { ok = false; break; }
         tc::fence_after();
-        const uint64_t dVh = dV0 + (uint64_t)s * kStage, dVl = dVh + kVB;
-        const uint32_t kcol = tbase + S::COL_C + (uint32_t)(b * 32);
+        const uint64_t dVh = dV0 + (uint64_t)s * (S::STAGE_BYTES >> 4), dVl = dVh + (S::V_BYTES >> 4);
+        const uint32_t kcol = tbase + (uint32_t)(b * 32);
 #pragma unroll
         for (int term = 0; term < 3; ++term) {
           const uint32_t A = kcol + (term == 2 ? 8u : 0u);   // K high | K low per 16 points
           const uint64_t B = term == 1 ? dVl : dVh;
 #pragma unroll
           for (int ks = 0; ks < kT2BN / 16; ++ks)
-            tc::mma_bf16_ts(tbase + S::COL_U, A + ks * 16, B + 16u * ks, idesc_u,
-                            (p | term | ks) != 0);
+            tc::mma_bf16_ts(tbase + S::COL_U, A + ks * 16, B + 16u * ks, idesc_u, (p | term | ks) != 0);
         }
         tc::commit(&empty[s]);
         if (p + NB < nt) {
@@ -299,32 +281,6 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
     const long long i = row0 + il;
     const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
     const float ai = a.params->c0f + a.bneg[i];   // bneg covers the padded rows (zero there)
-    if (half == 0) {
-      // set 0 writes this CTA's augmented rows A_i = [x^_i, 1, 0...] into tensor memory, as
-      // TF32 high parts (columns [0, K8)) and remainders ([K8, 2 K8)), 8 columns at a time;
-      // rows >= n are zero.  The same rounding as the B image (tf32_round) keeps the three
-      // products those of the augmented rows' split.
-      const bool in = i < a.n;
-#pragma unroll
-      for (int g = 0; g < K8 / 8; ++g) {
-        uint32_t hv[8], lv[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int k = 8 * g + e;
-          float v = 0.f;
-          if (in) v = k < a.DP ? a.xhat[i * a.DP + k] : (k == a.DP ? 1.f : 0.f);
-          const float h = tc::tf32_round(v);
-          hv[e] = __float_as_uint(h);
-          lv[e] = __float_as_uint(v - h);
-        }
-        tc::tmem_st8(tbase + lane_base + S::COL_A + 8 * g, hv);
-        tc::tmem_st8(tbase + lane_base + S::COL_A + K8 + 8 * g, lv);
-      }
-      tc::tmem_wait_st();
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(a_full);
-    }
     bool ok = true;
     for (int lt = half; lt < nt; lt += 2) {
       const int b = lt % NB;
@@ -333,7 +289,7 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
       tc::fence_after();
       // all 32 columns of C in one tensor-memory round trip; each pair's K high and low parts
       // are written back into the pair's own registers (no extra registers live)
-      const uint32_t ccol = tbase + lane_base + S::COL_C + (uint32_t)(b * 32);
+      const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32);
       uint32_t c[32];
       tc::tmem_ld16x2(ccol, c);
 #pragma unroll
@@ -401,11 +357,12 @@ __global__ void __launch_bounds__(kT2Threads, Tc2Shape<K8, N>::CTAS)
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  if (warp == 1) tc::tmem_dealloc(tbase, S::COLS);
+  if (warp == 1) tc::tmem_dealloc(tbase, kT2Cols);
   if (*s_fail) {
     if (tid == 0) {
       atomicOr(a.status, kStatusTimeout);
       // let the copies still in flight land before the CTA's shared memory goes away
+      (void)mbar_wait_bounded(a_full, 0);
       for (int lt2 = max(0, issued - S::ST); lt2 < issued; ++lt2)
         (void)mbar_wait_bounded(&full[lt2 % S::ST], (uint32_t)((lt2 / S::ST) & 1));
     }
@@ -448,7 +405,7 @@ struct Tc2Inst {
           cudaSuccess)
         smem_sm = 228 * 1024;
       const int by_smem = smem_sm / (int)(S::SMEM + 1024);
-      occ = std::max(1, std::min({by_smem, (int)(512 / S::COLS), S::CTAS}));
+      occ = std::max(1, std::min({by_smem, (int)(512 / kT2Cols), 4}));
     });
     return occ;
   }
@@ -471,8 +428,8 @@ struct Tc2Inst {
     const long long ntiles = (L.n + kT2BN - 1) / kT2BN;
     launch_pack_v(L, N, ntiles, s);
     Tc2DevArgs a;
-    a.xhat = L.xhat;
-    a.DP = L.DP;
+    a.A_hi = L.X_hi;
+    a.A_lo = L.X_lo;
     a.B_hi = L.X_hi + L.X_off;
     a.B_lo = L.X_lo + L.X_off;
     a.bneg = L.bneg;
@@ -528,8 +485,8 @@ cudaError_t launch_pack_x_tf32(const float* xhat, const float* bneg, const DevPa
   const int K8 = tc2_k8(DP);
   const long long total = ld128 * K8;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * num_sms);
-  pack_x_tf32_kernel<<<blocks, 256, 0, s>>>(xhat, bneg, params, DP, K8, n, ld128, X_hi + X_off,
-                                            X_lo + X_off);
+  pack_x_tf32_kernel<<<blocks, 256, 0, s>>>(xhat, bneg, params, DP, K8, n, ld128, X_hi, X_lo,
+                                            X_hi + X_off, X_lo + X_off);
   return cudaGetLastError();
 }
 

@@ -177,17 +177,6 @@ __device__ inline void mma_bf16_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdes
       : "memory");
 }
 
-// kind::tf32 with A in tensor memory (lane = row, one 32-bit element per column) and B in
-// shared memory: the A operand is not re-read from shared memory by every MMA.
-__device__ inline void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
-                                   uint32_t accumulate) {
-  asm volatile(
-      "{ .reg .pred p; setp.ne.b32 p, %4, 0; "
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p; }" ::"r"(dtmem),
-      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
 // Round to TF32 (nearest, ties away): the high part of a 3xTF32 split.
 __device__ inline float tf32_round(float x) {
   uint32_t y;
