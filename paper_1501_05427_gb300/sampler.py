@@ -193,11 +193,13 @@ def preconditioner_from_subset(X, y, psi0, m=500, seed=0):
 # A run
 # ------------------------------------------------------------------------------------------
 def run_sgld(ctx, psi0, n_steps, eps_first=1e-1, eps_last=1e-4, M=None, batch=100,
-             threshold=0.002, step0=0, prior_grad=None):
+             threshold=0.002, step0=0, prior_grad=None, record=None):
     """SGLD as Sec. 5.1 runs it: eps_t = a (b + t)^-1 from eps_first to eps_last, the Langevin
     monitor on batches of `batch` gradients, the step size frozen once the noise ratio is below
-    `threshold`.  ctx is a ulisse.Context (one ulisse_sgld_step per step).  Returns (trace of
-    psi, the monitor)."""
+    `threshold`.  ctx is a ulisse.Context (one ulisse_sgld_step per step).  prior_grad: None
+    (flat prior in psi), a vector, or a function of psi giving grad_psi log p(psi).  record:
+    None, or a list to which (t, eps_t, g~) is appended every step.  Returns (trace of psi,
+    the monitor)."""
     p = len(psi0)
     Mm = np.eye(p) if M is None else np.asarray(M, dtype=np.float64)
     a, b = step_size_schedule(eps_first, eps_last, n_steps)
@@ -207,9 +209,11 @@ def run_sgld(ctx, psi0, n_steps, eps_first=1e-1, eps_last=1e-4, M=None, batch=10
     eps_frozen = None
     for t in range(n_steps):
         eps_t = eps_frozen if eps_frozen is not None else step_size(a, b, t)
-        psi, g = ctx.sgld_step(psi, eps_t, step0 + t, M=None if M is None else Mm,
-                               prior_grad=prior_grad)
+        pg = prior_grad(psi) if callable(prior_grad) else prior_grad
+        psi, g = ctx.sgld_step(psi, eps_t, step0 + t, M=None if M is None else Mm, prior_grad=pg)
         trace[t] = psi
+        if record is not None:
+            record.append((t, eps_t, np.array(g)))
         if eps_frozen is None:
             eps_frozen = mon.update(t, eps_t, g)
     return trace, mon

@@ -119,3 +119,16 @@ def test_chosen_form_is_unbiased(orc):
     se = means.std(axis=0, ddof=1) / math.sqrt(len(means))
     z = (G.mean(axis=0) - g_exact) / se
     assert np.max(np.abs(z)) < 4.0, (G.mean(axis=0), g_exact, se)
+
+
+@pytest.mark.parametrize("precision", [u.PREC_MIXED, u.PREC_FP32])
+def test_warm_solves_after_autotune(precision):
+    """An autotuned context (the benchmark's form) warm-starts from its second step on: within
+    the first probe epoch every step needs far fewer K V rounds than the cold first one."""
+    prob = w.census_like(n=20_000, seed=778)
+    with _ctx(prob, n_probes=16, probe_refresh=20, warm_start_probes=1, seed=1,
+              precision=precision) as ctx:
+        ctx.autotune(prob.psi_true, 17, reps=2)
+        r = _steps_at_fixed_psi(ctx, prob.psi_true, 8)
+    print("autotuned, rounds per step in the first probe epoch: %s" % r.tolist())
+    assert np.all(r[1:] < 0.5 * r[0]), r
