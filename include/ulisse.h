@@ -222,6 +222,28 @@ ulisse_status ulisse_grad(ulisse_ctx *ctx, const double *psi, unsigned long long
                           double *g, ulisse_col_stats *stats);
 
 /*
+ * Posterior predictive for new inputs at parameters psi (Sec. 2, Eq. monte:carlo:integration):
+ *     p(y*_j | y, psi) = N(mean[j], var[j]),
+ *     mean[j] = k*_j^T K^{-1} y,   var[j] = sigma^2 + lambda - k*_j^T K^{-1} k*_j,
+ * k*_j = k_s(X, x*_j) the signal covariance between the training inputs and x*_j (var is
+ * that of a new noisy label; subtract lambda for the latent function).  K^{-1} y and, when
+ * var is requested, K^{-1} k*_j for every j come from one solve of the context's solver
+ * (configuration, precision and step as for ulisse_solve): with q > 0 they are ULISSE's
+ * unbiased estimates, so mean and the k*^T K^{-1} k* term are unbiased; with q = 0 every
+ * column runs to its convergence threshold and the result is the exact predictive up to it.
+ * Averaging N(mean, var) over posterior samples psi^(i) is the Monte Carlo estimate of the
+ * predictive distribution (paper_1501_05427_gb300.sampler.posterior_predictive).
+ *   psi    host, d + 2 doubles.
+ *   Xs     device, m x d row-major float test inputs.  m >= 1; m <= 1023 when var != NULL.
+ *   step   counter for the solver's random draws.
+ *   mean   device, m floats (output).   var  device, m floats (output), or NULL.
+ * Synchronises the stream.  Returns ULISSE_ERR_MAXITER / ULISSE_ERR_BREAKDOWN as ulisse_solve
+ * does (the outputs are still written).
+ */
+ulisse_status ulisse_predict(ulisse_ctx *ctx, const double *psi, const float *Xs, long long m,
+                             unsigned long long step, float *mean, float *var);
+
+/*
  * The fused gradient pass on its own (Eq. gradient:unbiased, Sec. 4.1): for every parameter
  * i = 0..d+1 (psi order: log l_1..log l_d, log sigma^2, log lambda),
  *     out[i] = sum_{m < M} scale[m] a_m^T (dK/dpsi_i) b_m,

@@ -390,6 +390,22 @@ def exact_gradient(X, y, psi):
     return g
 
 
+def predict(X, y, psi, Xs):
+    """Posterior predictive at new inputs Xs (Sec. 2): p(y*_j | y, psi) = N(mean_j, var_j),
+    mean_j = k*_j^T K^{-1} y, var_j = sigma^2 + lambda - k*_j^T K^{-1} k*_j, with k*_j the
+    signal covariance between X and x*_j, through the Cholesky factor of K."""
+    X = _f64(X)
+    Xs = _f64(Xs)
+    d = X.shape[1]
+    K = cov_matrix(X, psi)
+    L = np.linalg.cholesky(K)
+    Ks = cross_signal(X, Xs, psi)                   # n x m
+    a = _chol_solve(L, np.asarray(y, dtype=np.float64))
+    W = np.linalg.solve(L, Ks)                      # L^{-1} k*, so k*^T K^{-1} k* = |W_j|^2
+    sigma2, lam = np.exp(psi[d]), np.exp(psi[d + 1])
+    return Ks.T @ a, sigma2 + lam - np.sum(W * W, axis=0)
+
+
 def exact_trace_term(X, psi, i):
     """Tr(K^{-1} dK_i) through the Cholesky factor."""
     K = cov_matrix(X, psi)

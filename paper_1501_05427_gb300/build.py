@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libulisse.so")
 SOURCES = ["api.cu", "kmv_f32.cu", "kmv_f32_dp2.cu", "kmv_f32_dp4.cu", "kmv_f32_dp8.cu",
            "kmv_f32_dp16.cu", "kmv_f64.cu", "grad.cu", "kmv_noalloc.cu", "kmv_tc.cu",
-           "warm_start.cu", "batch_kmv.cu", "batch_grad.cu", "grad_tc.cu", "kmv_tc2.cu", "calib.cu"]
+           "warm_start.cu", "batch_kmv.cu", "batch_grad.cu", "grad_tc.cu", "kmv_tc2.cu", "calib.cu",
+           "predict.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

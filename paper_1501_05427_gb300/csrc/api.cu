@@ -137,6 +137,10 @@ struct ulisse_ctx {
   int b_np = 0;                    // packed parameter count
   int b_maxch = 1;                 // largest chunk count of the batched CG launches
 
+  // posterior predictive (ulisse_predict): the prescaled test inputs
+  void* pred_xs = nullptr;
+  size_t pred_xs_bytes = 0;
+
   // preconditioned CG (cfg.pcg_delta > 0): Z, X, Rr, P, KP (pcg_cap columns each)
   void* pcg_buf = nullptr;
   int pcg_cap = 0;
@@ -1187,6 +1191,61 @@ ulisse_status ulisse_grad(ulisse_ctx* ctx, const double* psi, unsigned long long
   CK(cudaMemcpyAsync(g, ctx->g_dev, sizeof(double) * (ctx->d + 2), cudaMemcpyDeviceToHost,
                      ctx->stream));
   CKS(copy_stats(ctx, stats, 1 + ctx->cfg.n_probes));
+  int st = 0;
+  CKS(read_status(ctx, &st));
+  return status_to_result(ctx, st);
+}
+
+extern "C++" {
+template <typename T>
+static ulisse_status predict_core(ulisse_ctx* ctx, const float* Xs, long long m,
+                                  unsigned long long step, float* mean, float* var) {
+  const int R = var ? 1 + (int)m : 1;
+  CKS(ensure_columns(ctx, R, R));
+  CK(cudaMemsetAsync(ctx->status_dev, 0, sizeof(int), ctx->stream));
+  CK(cudaMemsetAsync(ctx->warm_valid, 0, sizeof(int), ctx->stream));   // S is overwritten
+  const size_t xs_bytes = (size_t)m * ctx->DP * sizeof(T);
+  if (xs_bytes > ctx->pred_xs_bytes) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx->pred_xs);
+    ctx->pred_xs_bytes = 0;
+    CKS(dev_alloc(ctx, &ctx->pred_xs, xs_bytes));
+    ctx->pred_xs_bytes = xs_bytes;
+  }
+  CK(launch_predict_prescale<T>(Xs, m, ctx->d, ctx->DP, ctx->params, ctx->pred_xs,
+                                ctx->num_sms, ctx->stream));
+  // B[:, 0] = y and, for the variance, B[:, 1 + j] = k*_j = k_s(X, x*_j)
+  CK(cudaMemcpyAsync(ctx->B, ctx->y, ctx->ldn * ctx->esz, cudaMemcpyDeviceToDevice,
+                     ctx->stream));
+  if (var)
+    CK(launch_predict_cross_cols<T>(ctx->xhat, ctx->n, ctx->ldn, ctx->DP, ctx->pred_xs, m,
+                                    ctx->params, ctx->B, 1, ctx->stream));
+  int tot = 0;
+  CKS(upload_meta(ctx, R, nullptr, &tot));
+  ctx->meta_grad_R = -1;
+  CKS(solve_dispatch(ctx, R, 0, step));
+  CK(launch_predict_mean<T>(ctx->xhat, ctx->n, ctx->DP, ctx->pred_xs, m, ctx->params, ctx->SE,
+                            mean, ctx->stream));
+  if (var)
+    CK(launch_predict_var<T>(ctx->B, ctx->SE, ctx->n, ctx->ldn, 1, 1, m, ctx->params, var,
+                             ctx->stream));
+  ctx->launches += var ? 4 : 2;
+  return ULISSE_OK;
+}
+}  // extern "C++"
+
+ulisse_status ulisse_predict(ulisse_ctx* ctx, const double* psi, const float* Xs, long long m,
+                             unsigned long long step, float* mean, float* var) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: not supported");
+  if (!Xs || !mean || m < 1) return fail(ctx, ULISSE_ERR_ARG, "Xs/mean null or m < 1");
+  if (var && m > 1023)
+    return fail(ctx, ULISSE_ERR_ARG, "with the variance, at most 1023 test inputs per call");
+  if (m > (1LL << 26)) return fail(ctx, ULISSE_ERR_ARG, "m too large");
+  CKS(set_psi_host(ctx, psi));
+  CKS(prescale(ctx));
+  CKS(ctx->f64 ? predict_core<double>(ctx, Xs, m, step, mean, var)
+               : predict_core<float>(ctx, Xs, m, step, mean, var));
   int st = 0;
   CKS(read_status(ctx, &st));
   return status_to_result(ctx, st);
@@ -2702,7 +2761,7 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->part2), reinterpret_cast<void**>(&ctx->bneg),
                    &ctx->Vt_hi, &ctx->Vt_lo, &ctx->Gt_hi, &ctx->Gt_lo,
                    reinterpret_cast<void**>(&ctx->Xt_hi), reinterpret_cast<void**>(&ctx->Xt_lo),
-                   reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa, &ctx->pcg_buf,
+                   reinterpret_cast<void**>(&ctx->q_map), &ctx->q_sa, &ctx->pcg_buf, &ctx->pred_xs,
                    reinterpret_cast<void**>(&ctx->pcg_aux), reinterpret_cast<void**>(&ctx->pcg_live)})
     dev_free(*p);
   for (void** p : {reinterpret_cast<void**>(&ctx->X), &ctx->y, &ctx->xhat,

@@ -217,3 +217,40 @@ def run_sgld(ctx, psi0, n_steps, eps_first=1e-1, eps_last=1e-4, M=None, batch=10
         if eps_frozen is None:
             eps_frozen = mon.update(t, eps_t, g)
     return trace, mon
+
+
+# ------------------------------------------------------------------------------------------
+# Posterior predictive averaging (Sec. 2, Eq. monte:carlo:integration)
+# ------------------------------------------------------------------------------------------
+def posterior_predictive(ctx, psi_samples, Xs, step0=0, var=True):
+    """The Monte Carlo estimate of p(y* | y) = integral p(y* | y, theta) p(theta | y) dtheta:
+    for every posterior sample psi^(i) the library gives p(y* | y, psi^(i)) = N(mean_i, var_i)
+    (ulisse_predict, one solve per sample, step step0 + i for its random draws), and the
+    predictive is their equal-weight mixture.  Returns (means (N, m), variances (N, m) or None)
+    as numpy arrays; see mixture_moments and mixture_density for the mixture."""
+    means, varis = [], []
+    for i, psi in enumerate(np.asarray(psi_samples, dtype=np.float64)):
+        m, v = ctx.predict(psi, Xs, step=step0 + i, var=var)
+        means.append(m.cpu().numpy().astype(np.float64))
+        if var:
+            varis.append(v.cpu().numpy().astype(np.float64))
+    return np.array(means), (np.array(varis) if var else None)
+
+
+def mixture_moments(means, variances):
+    """Mean and variance of the equal-weight mixture of N(means[i], variances[i]) (per test
+    input): E[y*] = mean_i means, Var[y*] = mean_i (variances + means^2) - E[y*]^2 (the law of
+    total variance)."""
+    means = np.asarray(means, dtype=np.float64)
+    variances = np.asarray(variances, dtype=np.float64)
+    mu = means.mean(axis=0)
+    return mu, (variances + means * means).mean(axis=0) - mu * mu
+
+
+def mixture_density(y_star, means, variances):
+    """The Monte Carlo predictive density (1/N) sum_i N(y_star; means[i], variances[i]) at the
+    values y_star (one per test input)."""
+    means = np.asarray(means, dtype=np.float64)
+    variances = np.asarray(variances, dtype=np.float64)
+    z = (np.asarray(y_star, dtype=np.float64)[None, :] - means) ** 2 / variances
+    return (np.exp(-0.5 * z) / np.sqrt(2 * math.pi * variances)).mean(axis=0)

@@ -35,7 +35,7 @@ EXPORTED = [
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
     "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
-    "ulisse_selftest_wait_timeout", "ulisse_measure_ex2_rate",
+    "ulisse_selftest_wait_timeout", "ulisse_measure_ex2_rate", "ulisse_predict",
 ]
 
 
@@ -124,6 +124,7 @@ def load():
     lib.ulisse_dk_bilinear.argtypes = [P, P, P, P, I, P, P]
     lib.ulisse_selftest_wait_timeout.argtypes = [P]
     lib.ulisse_measure_ex2_rate.argtypes = [P, I, ctypes.POINTER(D), ctypes.POINTER(D)]
+    lib.ulisse_predict.argtypes = [P, P, P, LL, U64, P, P]
     lib.ulisse_sgld_step.argtypes = [P, P, D, P, P, U64, P]
     lib.ulisse_sgld_chain.argtypes = [P, P, P, I, P, P, U64, P]
     lib.ulisse_counters.argtypes = [P, ctypes.POINTER(LL), ctypes.POINTER(D), ctypes.POINTER(LL)]
@@ -295,6 +296,23 @@ class Context:
                                                  ctypes.c_void_p(Bc.data_ptr()), M, _hptr(sc),
                                                  _hptr(out)))
         return out
+
+    def predict(self, psi, Xs, step=0, var=True, allow=()):
+        """Posterior predictive at psi for the test inputs Xs ((m, d) CUDA tensor): returns
+        (mean, var) as CUDA tensors of m floats (var None when not requested)."""
+        import torch
+        Xs = Xs.contiguous().float()
+        m = Xs.shape[0]
+        if Xs.dim() != 2 or Xs.shape[1] != self.d:
+            raise ValueError("Xs must be (m, d)")
+        mean = torch.empty(m, dtype=torch.float32, device=Xs.device)
+        v = torch.empty(m, dtype=torch.float32, device=Xs.device) if var else None
+        psi = _f64_host(psi, self.p)
+        self._check(self._lib.ulisse_predict(self._h, _hptr(psi), ctypes.c_void_p(Xs.data_ptr()), m,
+                                             step, ctypes.c_void_p(mean.data_ptr()),
+                                             ctypes.c_void_p(v.data_ptr()) if var else None),
+                    allow)
+        return mean, v
 
     def sgld_step(self, psi, eps_t, step, M=None, prior_grad=None, allow=()):
         """One SGLD step; returns (psi_new, g) as numpy arrays."""

@@ -109,3 +109,8 @@ def test_measure_ex2_rate_rejects_bad_arguments(lib):
     r = ctypes.c_double()
     assert lib.ulisse_measure_ex2_rate(None, 0, ctypes.byref(r), None) == ulisse.ULISSE_ERR_ARG
     assert lib.ulisse_measure_ex2_rate(None, 5, None, None) == ulisse.ULISSE_ERR_ARG
+
+
+def test_predict_rejects_bad_arguments(lib):
+    from paper_1501_05427_gb300 import ulisse
+    assert lib.ulisse_predict(None, None, None, 1, 0, None, None) == ulisse.ULISSE_ERR_ARG

@@ -851,3 +851,59 @@ def test_ulisse_on_pcg_expectation_by_enumeration(orc):
             ref += pcg.weight(j, beta) * (S[l + j] - S[l + j - 1])
         assert st[c, 0] == l and st[c, 1] == min(l + J, T)
         assert np.linalg.norm(Sest[:, c] - ref) < 1e-12 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------------------------------
+# Posterior predictive (oracle.predict; Sec. 2, Eq. monte:carlo:integration)
+# ----------------------------------------------------------------------------------------
+def test_predict_single_training_point(orc):
+    """n = 1: mean = k_s(x*, x1) y1 / (sigma^2 + lambda), var = sigma^2 + lambda -
+    k_s(x*, x1)^2 / (sigma^2 + lambda), k_s = sigma^2 exp(-1/2 sum (x* - x1)^2 / l^2)."""
+    psi = np.log([0.5, 2.0, 1.5, 0.2])
+    X = np.array([[0.3, -0.4]])
+    y = np.array([1.7])
+    Xs = np.array([[0.1, 0.6], [0.3, -0.4]])
+    mean, var = orc.predict(X, y, psi, Xs)
+    s2, lam = 1.5, 0.2
+    for j in range(2):
+        k = s2 * math.exp(-0.5 * ((Xs[j, 0] - 0.3) ** 2 / 0.25 + (Xs[j, 1] + 0.4) ** 2 / 4.0))
+        assert abs(mean[j] - k * 1.7 / (s2 + lam)) < 1e-14
+        assert abs(var[j] - (s2 + lam - k * k / (s2 + lam))) < 1e-14
+
+
+def test_predict_matches_sklearn(orc):
+    """An independent implementation: scikit-learn's Gaussian-process regressor with the same
+    fixed covariance (ConstantKernel sigma^2 x RBF(l) + WhiteKernel(lambda), no optimisation)
+    gives the same predictive mean and, with the noise kernel at the test input, the same
+    variance of a new label."""
+    gp = pytest.importorskip("sklearn.gaussian_process")
+    kern = pytest.importorskip("sklearn.gaussian_process.kernels")
+    rng = np.random.default_rng(31)
+    X = rng.uniform(0, 1, (60, 3))
+    y = np.sin(4 * X[:, 0]) + 0.3 * rng.standard_normal(60)
+    psi = np.log([0.3, 0.5, 0.8, 1.3, 0.05])
+    Xs = rng.uniform(0, 1, (25, 3))
+    k = (kern.ConstantKernel(1.3, "fixed") * kern.RBF([0.3, 0.5, 0.8], "fixed")
+         + kern.WhiteKernel(0.05, "fixed"))
+    reg = gp.GaussianProcessRegressor(kernel=k, optimizer=None, alpha=0.0, normalize_y=False)
+    reg.fit(X, y)
+    m_ref, sd_ref = reg.predict(Xs, return_std=True)
+    mean, var = orc.predict(X, y, psi, Xs)
+    assert np.max(np.abs(mean - m_ref)) < 1e-8 * max(1.0, np.max(np.abs(m_ref)))
+    assert np.max(np.abs(var - sd_ref ** 2)) < 1e-8
+
+
+def test_predict_at_training_inputs(orc):
+    """At a training input the mean is the smoothed value (K_s K^{-1} y)_i and the latent
+    variance (var - lambda) is the posterior variance diag(K_s - K_s K^{-1} K_s)_i -- the
+    textbook smoother, formed here from the dense matrices with numpy."""
+    X = _rand_X(40, 2, 32)
+    psi = np.log([0.3, 0.4, 1.0, 0.1])
+    y = np.random.default_rng(32).standard_normal(40)
+    K = orc.cov_matrix(X, psi)
+    Ks = K - 0.1 * np.eye(40)
+    mean, var = orc.predict(X, y, psi, X[[3, 17]])
+    sm = Ks @ np.linalg.solve(K, y)
+    pv = np.diag(Ks - Ks @ np.linalg.solve(K, Ks))
+    assert np.allclose(mean, sm[[3, 17]], rtol=0, atol=1e-12)
+    assert np.allclose(var - 0.1, pv[[3, 17]], rtol=0, atol=1e-12)

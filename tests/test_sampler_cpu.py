@@ -132,3 +132,53 @@ def test_run_sgld_freezes_the_step_size():
     # frozen where eps/4 * s2 (the exact ratio here) first drops below 0.002, within the
     # batch's sampling error
     assert ctx.eps[t0] / 4 * 5.0 < 0.002 * 1.5
+
+
+def test_mixture_moments_and_density():
+    """The equal-weight mixture of Gaussians: its moments by the law of total variance agree
+    with a large sample drawn from the mixture, and its density integrates to one and equals
+    scipy's normal pdf averaged by hand."""
+    from scipy.stats import norm
+    from paper_1501_05427_gb300 import sampler
+    rng = np.random.default_rng(4)
+    means = rng.standard_normal((7, 3))
+    varis = rng.uniform(0.1, 2.0, (7, 3))
+    mu, v = sampler.mixture_moments(means, varis)
+    k = rng.integers(0, 7, 400_000)
+    draws = means[k] + np.sqrt(varis[k]) * rng.standard_normal((400_000, 3))
+    assert np.all(np.abs(draws.mean(axis=0) - mu) < 5 * np.sqrt(v / 400_000))
+    assert np.all(np.abs(draws.var(axis=0) / v - 1) < 0.02)
+    ys = np.array([0.3, -1.0, 2.0])
+    ref = np.mean([norm.pdf(ys, means[i], np.sqrt(varis[i])) for i in range(7)], axis=0)
+    assert np.allclose(sampler.mixture_density(ys, means, varis), ref, rtol=1e-12)
+    grid = np.linspace(-15, 15, 60001)
+    dens = np.array([sampler.mixture_density(np.full(3, g), means, varis) for g in grid])
+    assert np.allclose(np.trapezoid(dens, grid, axis=0), 1.0, atol=1e-6)
+
+
+def test_posterior_predictive_calls_predict_per_sample():
+    from paper_1501_05427_gb300 import sampler
+
+    class FakeTensor:
+        def __init__(self, a):
+            self.a = a
+
+        def cpu(self):
+            return self
+
+        def numpy(self):
+            return self.a
+
+    class FakeCtx:
+        def __init__(self):
+            self.calls = []
+
+        def predict(self, psi, Xs, step=0, var=True):
+            self.calls.append((psi.copy(), step))
+            return FakeTensor(np.full(2, psi[0])), FakeTensor(np.full(2, 1.0 + step)) if var else None
+
+    ctx = FakeCtx()
+    psis = np.array([[0.5, 0.0], [1.5, 0.0]])
+    m, v = sampler.posterior_predictive(ctx, psis, None, step0=10)
+    assert [c[1] for c in ctx.calls] == [10, 11]
+    assert np.allclose(m, [[0.5, 0.5], [1.5, 1.5]]) and np.allclose(v, [[11, 11], [12, 12]])
