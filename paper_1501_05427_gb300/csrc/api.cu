@@ -10,6 +10,7 @@
 #include "../../include/ulisse.h"
 #include "solver_kernels.cuh"
 #include "pcg_kernels.cuh"
+#include "predict.cuh"
 #include "warm_start.cuh"
 #include "batch.cuh"
 

@@ -9,7 +9,7 @@
 // samples theta^(i) is the Monte Carlo estimate of Eq. monte:carlo:integration.
 #include <algorithm>
 
-#include "ulisse_internal.cuh"
+#include "predict.cuh"
 
 namespace ulisse {
 
