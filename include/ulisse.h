@@ -165,16 +165,38 @@ ulisse_status ulisse_kmv_f64(ulisse_ctx *ctx, const double *psi, int which, cons
  * 64) x (d rounded up to 2, 4, 8 or 16, plus R) floats must fit in 16 MiB (for d = 8 and
  * R = 17, n <= 167,000); larger requests return ULISSE_ERR_ARG without touching the GPU.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
- * with that device current); make that first call before any stream capture.
+ * with that device current); make that first call before any stream capture.  Do not
+ * capture this call in a CUDA graph at all: psi is copied from (possibly pageable) host
+ * memory when the call is made, and a captured copy would read the host buffer again at each
+ * replay.
  * All calls share the array: each call clears the parts that must start at zero, but two
  * calls whose GPU work overlaps (different streams, or different host threads) race on it
  * and may return wrong results.  Serialise them.
+ * The split of the j range is planned for the SMs whose partial sums fit the array (about
+ * 48 MiB / 2 MiB per SM, so ~23 SMs' worth of splits), fewer than ulisse_kmv would use: for
+ * small and medium n the call runs below ulisse_kmv's throughput.
  * Errors: ULISSE_ERR_ARG (null pointer, sizes out of range or too large, non-finite psi),
- * ULISSE_ERR_CUDA (no device, or a launch or copy failed).  Device-side timeouts of the
- * bounded waits are not reported by this call.
+ * ULISSE_ERR_CUDA (no device, or a launch or copy failed).  The call returns before the GPU
+ * work ends, so a bounded device wait that runs out (after about a second, i.e. when the GPU
+ * is stalled) is not in its return value: the kernel records it in the array's status word
+ * and U is then undefined.  ulisse_kmv_noalloc_status reads that word back.
  */
 ulisse_status ulisse_kmv_noalloc(const float *X, long long n, int d, const double *psi,
                                  int which, const float *V, int R, float *U, void *stream);
+
+/*
+ * Outcome of the device work of the last ulisse_kmv_noalloc call on the current device.
+ * Each ulisse_kmv_noalloc call clears the status word (on its stream) before its kernels;
+ * this call copies the word to host memory on `stream` and synchronises that stream, so
+ * pass the stream of the call being checked (or synchronise the device first).  It
+ * allocates nothing.
+ *   stream  cudaStream_t (as void*).
+ *   status  host int: 0 = every wait ended, else the timeout flags the kernels set.
+ * Returns ULISSE_OK (status 0), ULISSE_ERR_TIMEOUT (a bounded wait ran out: U of that call is
+ * undefined), ULISSE_ERR_ARG (status is null), ULISSE_ERR_CUDA (no device, or the copy
+ * failed).
+ */
+ulisse_status ulisse_kmv_noalloc_status(void *stream, int *status);
 
 /* Per-column outcome of a solve, written to host memory when requested. */
 typedef struct {

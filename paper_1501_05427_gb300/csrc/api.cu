@@ -1109,7 +1109,7 @@ static ulisse_status kmv_common(ulisse_ctx* ctx, const double* psi, int which, c
   int mode = kModeK, w = -1;
   if (which >= 0 && which < ctx->d) { mode = kModeDLen; w = which; }
   else if (which == ctx->d) mode = kModeDSig;
-  else if (which == ctx->d + 1) mode = 3;
+  else if (which == ctx->d + 1) mode = kModeDLam;
   CKS(run_kmv(ctx, ctx->D, ctx->iota, R, ctx->KD, ctx->iota, mode, w));
   if (ctx->esz == ue) {
     CK(cudaMemcpy2DAsync(U, n * ue, ctx->KD, ctx->ldn * ctx->esz, n * ue, R,

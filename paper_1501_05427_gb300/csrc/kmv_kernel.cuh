@@ -69,7 +69,7 @@ __device__ __forceinline__ T kernel_from_dist(T dist, float c0, float c1, double
 }
 
 // MODE (compile time): kModeK (K), kModeDLen (dK/dlog l_which), kModeDSig (dK/dlog sigma^2),
-// 3 (dK/dlog lambda = lambda I: no tiles, only the diagonal term).
+// kModeDLam (dK/dlog lambda = lambda I: no tiles, only the diagonal term).
 template <typename T, int DP, int R, int TM, int NT, int MODE>
 __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   constexpr int BM = NT * TM;
@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   const long long row0 = (long long)rb * BM;
   const int tile_begin = sp * a.tiles_per_split;
   const int tile_end = min(tile_begin + a.tiles_per_split, a.ntiles);
-  const int nt_local = (MODE == 3) ? 0 : max(0, tile_end - tile_begin);
+  const int nt_local = (MODE == kModeDLam) ? 0 : max(0, tile_end - tile_begin);
   const int Ra = a.R;
 
   const float c0 = a.params->c0f, c1 = a.params->c1f;
@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(NT) kmv_kernel(const KmvDevArgs<T> a) {
   }
 
   // Diagonal term lambda V (K) or the whole product (dK/dlog lambda = lambda I).
-  constexpr bool add_diag = (MODE == kModeK || MODE == 3);
+  constexpr bool add_diag = (MODE == kModeK || MODE == kModeDLam);
   if (a.nsplit == 1) {
 #pragma unroll
     for (int t = 0; t < TM; ++t) {

@@ -38,7 +38,7 @@ struct KmvInst {
   }
   static cudaError_t launch(KmvLaunch& L, cudaStream_t s) {
     KmvPlan p = plan(L);
-    if (MODE == 3) {  // dK/dlog lambda = lambda I: no tiles, one CTA per row block
+    if (MODE == kModeDLam) {  // dK/dlog lambda = lambda I: no tiles, one CTA per row block
       p.nsplit = 1;
       p.tiles_per_split = 0;
       p.partial_bytes = 0;
@@ -103,7 +103,7 @@ cudaError_t dispatch_mode(KmvLaunch& L, cudaStream_t s) {
       return dispatch_r<T, DP, TMK, kModeK>(L, s, RK{});
     case kModeDLen: return dispatch_r<T, DP, TMK, kModeDLen>(L, s, RD{});
     case kModeDSig: return dispatch_r<T, DP, TMK, kModeDSig>(L, s, RD{});
-    case 3: return dispatch_r<T, DP, TMK, 3>(L, s, RD{});
+    case kModeDLam: return dispatch_r<T, DP, TMK, kModeDLam>(L, s, RD{});
     default: return cudaErrorInvalidValue;
   }
 }

@@ -48,6 +48,12 @@ std::mutex g_setup_mutex;
 DeviceScratch g_scratch[kNoAllocMaxDevices];
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
+// Fixed head of the scratch array: DevParams, psi, then the status word the kernels set when a
+// bounded wait runs out.
+constexpr size_t kParamsOff = (sizeof(DevParams) + kAlign - 1) / kAlign * kAlign;
+constexpr size_t kStatusOff = (kParamsOff + sizeof(double) * kMaxP + kAlign - 1) / kAlign * kAlign;
+int* status_word(const DeviceScratch* sc) { return reinterpret_cast<int*>(sc->base + kStatusOff); }
+
 // The reason is documented at each call site; only the status code leaves the library.
 ulisse_status fail(const char* /*reason*/, ulisse_status s) { return s; }
 
@@ -104,14 +110,12 @@ extern "C" ulisse_status ulisse_kmv_noalloc(const float* X, long long n, int d, 
   if (st != ULISSE_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
-  // Layout of the scratch array for this call.
-  size_t off = 0;
-  DevParams* params = reinterpret_cast<DevParams*>(sc->base + off);
-  off = align_up(off + sizeof(DevParams));
-  double* psi_dev = reinterpret_cast<double*>(sc->base + off);
-  off = align_up(off + sizeof(double) * kMaxP);
-  int* status = reinterpret_cast<int*>(sc->base + off);
-  off = align_up(off + sizeof(int));
+  // Layout of the scratch array for this call (the head, up to the status word, is the
+  // same for every call: ulisse_kmv_noalloc_status reads the word there).
+  DevParams* params = reinterpret_cast<DevParams*>(sc->base);
+  double* psi_dev = reinterpret_cast<double*>(sc->base + kParamsOff);
+  int* status = status_word(sc);
+  size_t off = align_up(kStatusOff + sizeof(int));
   int* counters = reinterpret_cast<int*>(sc->base + off);
   off = align_up(off + kNoAllocCounterBytes);
   float* xhat = reinterpret_cast<float*>(sc->base + off);
@@ -171,7 +175,7 @@ extern "C" ulisse_status ulisse_kmv_noalloc(const float* X, long long n, int d, 
   } else if (which == d) {
     L.mode = kModeDSig;
   } else if (which == d + 1) {
-    L.mode = 3;
+    L.mode = kModeDLam;
   }
   L.partials = partials;
   L.partials_bytes = partial_bytes;
@@ -183,4 +187,20 @@ extern "C" ulisse_status ulisse_kmv_noalloc(const float* X, long long n, int d, 
   if (e == cudaErrorMemoryAllocation)
     return fail("split-j partial sums do not fit the static scratch", ULISSE_ERR_ARG);
   return ck(e, "K V launch failed");
+}
+
+extern "C" ulisse_status ulisse_kmv_noalloc_status(void* stream, int* status) {
+  if (!status) return fail("status must not be null", ULISSE_ERR_ARG);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail("no current CUDA device", ULISSE_ERR_CUDA);
+  DeviceScratch* sc = nullptr;
+  ulisse_status st = setup_device(dev, &sc);
+  if (st != ULISSE_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  if (cudaMemcpyAsync(&h, status_word(sc), sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail("read-back of the status word failed", ULISSE_ERR_CUDA);
+  *status = h;
+  return h == 0 ? ULISSE_OK : ULISSE_ERR_TIMEOUT;
 }

@@ -199,7 +199,8 @@ __device__ inline double block_sum(double v, double* scratch /* >= NT/32 */) {
 // ------------------------------------------------------------------------------------
 // Launch descriptors.
 // ------------------------------------------------------------------------------------
-enum KmvMode { kModeK = 0, kModeDLen = 1, kModeDSig = 2 };
+// kModeDLam: dK/dlog lambda = lambda I (no tiles, only the diagonal term).
+enum KmvMode { kModeK = 0, kModeDLen = 1, kModeDSig = 2, kModeDLam = 3 };
 
 // Where the mixed path forms the cross term x^_i . x^_j (ulisse_config.tc_cross_term).
 constexpr int kCrossPipe = 1;     // FP32 FMAs in the epilogue (kmv_tc_kernel)

@@ -31,7 +31,7 @@ EXPORTED = [
     "ulisse_config_default", "ulisse_create", "ulisse_create_host", "ulisse_kmv",
     "ulisse_kmv_f64", "ulisse_solve", "ulisse_grad", "ulisse_sgld_step", "ulisse_sgld_chain",
     "ulisse_counters", "ulisse_profile_enable", "ulisse_profile_read", "ulisse_last_error",
-    "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
+    "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_kmv_noalloc_status", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
     "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
@@ -131,6 +131,7 @@ def load():
     lib.ulisse_profile_enable.argtypes = [P, I]
     lib.ulisse_profile_read.argtypes = [P, ctypes.POINTER(ulisse_profile), I]
     lib.ulisse_kmv_noalloc.argtypes = [P, LL, I, P, I, P, I, P, P]
+    lib.ulisse_kmv_noalloc_status.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
     lib.ulisse_ws_init.argtypes = [P, ctypes.POINTER(ulisse_ws_config)]
     lib.ulisse_ws_set.argtypes = [P, I, I]
     lib.ulisse_ws_train.argtypes = [P, I, I, D, ctypes.POINTER(D)]
@@ -579,6 +580,19 @@ def ulisse_kmv_noalloc(X, psi, V, which=-1, out=None, stream=None):
     if st != ULISSE_OK:
         raise UlisseError(st, "ulisse_kmv_noalloc rejected the call")
     return out[:, 0] if V.dim() == 1 else out
+
+
+def ulisse_kmv_noalloc_status(stream=None):
+    """Status word of the last ulisse_kmv_noalloc call's device work (0: every bounded wait
+    ended); synchronises `stream`.  Raises UlisseError on a timeout or a CUDA error."""
+    import torch
+    lib = load()
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    word = ctypes.c_int(-1)
+    st = lib.ulisse_kmv_noalloc_status(ctypes.c_void_p(stream.cuda_stream), ctypes.byref(word))
+    if st != ULISSE_OK:
+        raise UlisseError(st, "ulisse_kmv_noalloc: status word %d" % word.value)
+    return word.value
 
 
 def ulisse_measure_ex2_rate(stream=None, reps=5):

@@ -23,6 +23,13 @@ from paper_1501_05427_gb300 import workloads as w  # noqa: E402
 TOL = 1e-5   # the K V parity tolerance used for the context-based entry point
 
 
+@pytest.fixture(scope="module")
+def orc():
+    import oracle
+    oracle.build()
+    return oracle
+
+
 def _noalloc(lib, X, psi, which, V):
     n, d = X.shape
     R = V.shape[1]
@@ -52,7 +59,7 @@ def _close(a, b):
     assert torch.linalg.norm(a - b).item() <= TOL * torch.linalg.norm(b).item()
 
 
-def test_noalloc_matches_context_entry_point_twice():
+def test_noalloc_matches_context_entry_point_twice(orc):
     lib = u.load()
     cases = [
         (w.census_like(n=9_937, d=8, seed=3), -1, 17),   # ragged n, many right-hand sides
@@ -63,8 +70,17 @@ def test_noalloc_matches_context_entry_point_twice():
         y = torch.from_numpy(prob.y).cuda()
         V = torch.randn((prob.n, R), device="cuda")
         got = _noalloc(lib, X, prob.psi_true, which, V)
+        assert u.ulisse_kmv_noalloc_status() == 0
         ref = _reference(prob, X, y, which, V)
         _close(got, ref)
+        # and on its own against the oracle, row by row (FP64, rows evaluated one by one)
+        rows = np.unique(np.r_[0, prob.n - 1, np.random.default_rng(9).integers(0, prob.n, 14)])
+        Vd = V.double().cpu().numpy()
+        want = orc.kmv_rows(prob.X.astype(np.float64), prob.psi_true, Vd, rows, which)
+        scale = orc.kmv_rows(prob.X.astype(np.float64), prob.psi_true, Vd, rows, which,
+                             absolute=True)
+        err = np.abs(got.double().cpu().numpy()[rows] - want)
+        assert np.all(err <= TOL * np.maximum(scale, 1e-30))
 
 
 def test_noalloc_rejects_oversized_requests():
