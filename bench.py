@@ -845,6 +845,9 @@ def run_ours(args):
         "grad_ms_per_step": prof["grad_ms"] / prof["steps"],
         "grad_tflops": (prof["grad_flop"] / (prof["grad_ms"] / 1e3) / 1e12
                         if prof["grad_ms"] > 0 else None),
+        "grad_flop_per_launch": ("n(n+1)/2 (5d + 4 + 4M): each unordered pair once, 2M factor "
+                                 "products" if args.path == "mixed"
+                                 else "n^2 (5d + 4 + 2M): every ordered pair"),
     })
     extras = {}
     if world == 1 and not args.no_extras:

@@ -823,8 +823,14 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M, const int* amap = nullptr,
                     : ctx->mixed ? launch_grad_tc(L, ctx->stream)
                                  : launch_grad_f32(L, ctx->stream);
     if (ctx->prof) {
-      if (e == cudaSuccess && !ctx->planning)
-        prof_end(ctx, 1, ea, eb, (double)ctx->n * ctx->n * (5.0 * ctx->d + 4.0 + 2.0 * M));
+      if (e == cudaSuccess && !ctx->planning) {
+        // the tensor-core pass visits each unordered pair once with 2M factor products; the
+        // SIMT passes visit every ordered pair with M
+        const double nn = (double)ctx->n;
+        const double flop = ctx->mixed ? nn * (nn + 1.0) / 2.0 * (5.0 * ctx->d + 4.0 + 4.0 * M)
+                                       : nn * nn * (5.0 * ctx->d + 4.0 + 2.0 * M);
+        prof_end(ctx, 1, ea, eb, flop);
+      }
       else
         ctx->free_events.push_back({ea, eb});
     }
@@ -986,8 +992,8 @@ static ulisse_status create_impl(ulisse_ctx** out, const float* X, const float* 
     if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->bneg), sizeof(float) * ctx->ld128)) ||
         (s = dev_alloc(ctx, &ctx->Vt_hi, 2 * ctx->ld128 * 64)) ||
         (s = dev_alloc(ctx, &ctx->Vt_lo, 2 * ctx->ld128 * 64)) ||
-        (s = dev_alloc(ctx, &ctx->Gt_hi, 2 * ctx->ld128 * 112)) ||
-        (s = dev_alloc(ctx, &ctx->Gt_lo, 2 * ctx->ld128 * 112)) ||
+        (s = dev_alloc(ctx, &ctx->Gt_hi, 2 * ctx->ld128 * kGtScratchRows)) ||
+        (s = dev_alloc(ctx, &ctx->Gt_lo, 2 * ctx->ld128 * kGtScratchRows)) ||
         (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->Xt_hi), 4 * ctx->ld128 * 48)) ||
         (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->Xt_lo), 4 * ctx->ld128 * 48)))
       return bail(s);

@@ -3,13 +3,23 @@
 //     g~_i = sum_m a_m^T dK_i b_m
 // for all parameters at once, through W_ij = sum_m a_m[i] b_m[j] and P_ij = k_s(i,j) W_ij:
 //     g~_{log l_k}     = sum_ij P_ij (x^_ik - x^_jk)^2
-//                      = sum_i [ x^_ik^2 S_i - 2 x^_ik G_ik + H_ik ],
-//                        S_i = sum_j P_ij,  G_ik = sum_j P_ij x^_jk,  H_ik = sum_j P_ij x^_jk^2
-//     g~_{log sigma^2} = sum_i S_i
+//     g~_{log sigma^2} = sum_ij P_ij
 //     g~_{log lambda}  = lambda sum_i W_ii.
-// For a block of 128 rows I and each 32-point tile J:
-//   1. W_IJ = A^_I B^_J^T on the tensor cores (K = the factor index m, A^ = scaled a-columns,
-//      both split into BF16 high + low parts: three products), into tensor memory;
+// Both double sums weigh the pair (i, j) by a symmetric function (k_s and the squared
+// difference), so they take each unordered pair once with the symmetric weight
+//     W'_ij = W_ij + W_ji = [A^_i | b_i] . [b_j | A^_j]     (A^ = the scaled a-columns),
+// a product over 2M factors: the pass visits, for the block of 128 rows I, only the 32-point
+// tiles J at or after the block's own points (J >= I), with weight 1/2 on the four tiles of
+// I itself (there both (i, j) and (j, i) are visited).  With P'_ij = k_s(i,j) W'_ij on the
+// visited pairs,
+//     g~_{log l_k}     = sum_i [ x^_ik^2 S_i - 2 x^_ik G_ik + H_ik ],
+//                        S_i = sum_j P'_ij,  G_ik = sum_j P'_ij x^_jk,  H_ik = sum_j P'_ij x^_jk^2
+//     g~_{log sigma^2} = sum_i S_i,
+// so half the kernel values of the full square are formed.  Nothing is written per point j,
+// which is why the symmetry is free here (a K V product would have to add K_IJ^T V_I to the
+// rows of J).  For a block of 128 rows I and each visited 32-point tile J:
+//   1. W'_IJ = [A^ | B]_I [B | A^]_J^T on the tensor cores (K = 2M factors, both operands
+//      split into BF16 high + low parts: three products), into tensor memory;
 //   2. the epilogue warps read W back (tcgen05.ld), form the kernel values as the K V kernel
 //      does (cross term from row norms, one ex2), multiply, split P into BF16 high + low parts
 //      and store them over W's own tensor-memory columns;
@@ -35,18 +45,22 @@ constexpr int kGtBN = 32;
 constexpr int kGtBM = 128;
 constexpr int kGtThreads = 320;    // warp 0 producer, warp 1 MMA issuer, warps 2-9 epilogue
 constexpr uint32_t kGtCols = 128;  // tensor-memory columns per CTA
-constexpr int kGtZOff = 64;        // Z image offset in the packed scratch, in units of ld128
+constexpr int kGtZOff = 128;       // Z image offset in the packed scratch, in units of ld128
+static_assert(16 * 8 <= kGtZOff && kGtZOff + 48 <= kGtScratchRows,
+              "operand images exceed the gradient scratch");
 
 __device__ inline void split_bf16(float v, __nv_bfloat16& h, __nv_bfloat16& l) {
   h = __float2bfloat16_rn(v);
   l = __float2bfloat16_rn(v - __bfloat162float(h));
 }
 
-// Right factors b_m (m < M) of every 32-point tile as BF16 high and low parts: a K-major
-// canonical image of 32 points (rows) x K1 factors; factors m >= M and points j >= n are zero.
-__global__ void pack_bt_kernel(const float* __restrict__ B, long long ld,
-                               const int* __restrict__ bmap, int M, int K1, long long n,
-                               long long ntiles, __nv_bfloat16* __restrict__ Bhi,
+// Right operand [b_j | A^_j] of every 32-point tile as BF16 high and low parts: a K-major
+// canonical image of 32 points (rows) x K1 factor slots, slot m < M holding b_m[j] and slot
+// M + m holding sa[m] a_m[j]; slots >= 2M and points j >= n are zero.
+__global__ void pack_bt_kernel(const float* __restrict__ B, const int* __restrict__ bmap,
+                               const float* __restrict__ A, const int* __restrict__ amap,
+                               const float* __restrict__ sa, long long ld, int M, int K1,
+                               long long n, long long ntiles, __nv_bfloat16* __restrict__ Bhi,
                                __nv_bfloat16* __restrict__ Blo) {
   const long long per_tile = (long long)kGtBN * K1;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntiles * per_tile;
@@ -55,7 +69,11 @@ __global__ void pack_bt_kernel(const float* __restrict__ B, long long ld,
     const int rem = (int)(idx - t * per_tile);
     const int m = rem / kGtBN, j = rem - m * kGtBN;
     const long long jj = t * kGtBN + j;
-    const float v = (m < M && jj < n) ? B[(long long)bmap[m] * ld + jj] : 0.f;
+    float v = 0.f;
+    if (jj < n) {
+      if (m < M) v = B[(long long)bmap[m] * ld + jj];
+      else if (m < 2 * M) v = sa[m - M] * A[(long long)amap[m - M] * ld + jj];
+    }
     __nv_bfloat16 h, l;
     split_bf16(v, h, l);
     const long long off = t * per_tile + tc::canon_offset(j, m, 2, K1 / 8) / 2;
@@ -112,7 +130,7 @@ struct GtDevArgs {
   long long n;
   int d;
   const DevParams* params;
-  int nsplit, tiles_per_split, ntiles;
+  int nsplit, ntiles;
   double* partials;
   int* counter;
   double* g_out;
@@ -121,7 +139,7 @@ struct GtDevArgs {
 
 template <int DP, int KS>
 struct GtShape {
-  static constexpr int K1 = 16 * KS;                   // factor dimension, padded
+  static constexpr int K1 = 16 * KS;                   // factor slots (2M), padded
   static constexpr int N2 = (2 * DP + 1 + 15) / 16 * 16;
   static constexpr int ST = 4;
   static constexpr uint32_t A_BYTES = kGtBM * K1 * 2;  // one part of A^_I
@@ -168,17 +186,28 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   auto stage = [&](int s) -> unsigned char* { return smem + S::OFF_STAGES + s * S::STAGE_BYTES; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // Row block rb visits the tiles [4 rb, ntiles) (its own four tiles, then every later
+  // one), cut into nsplit equal ranges; CTAs start in row-block order, longest ranges first.
+  constexpr int kTilesPerBlock = kGtBM / kGtBN;
   const int rb = blockIdx.x / a.nsplit;
   const int sp = blockIdx.x - rb * a.nsplit;
   const long long row0 = (long long)rb * kGtBM;
-  const int tile_begin = sp * a.tiles_per_split;
-  const int nt = max(0, min(tile_begin + a.tiles_per_split, a.ntiles) - tile_begin);
+  const int diag_end = min(kTilesPerBlock * (rb + 1), a.ntiles);   // tiles of I itself
+  const int span = a.ntiles - kTilesPerBlock * rb;
+  const int per = (span + a.nsplit - 1) / a.nsplit;
+  const int tile_begin = kTilesPerBlock * rb + sp * per;
+  const int nt = max(0, min(tile_begin + per, a.ntiles) - tile_begin);
 
-  // A^_I = sa[m] a_m[i], split into BF16 high and low parts (K-major canonical image).
+  // [A^_I | B_I]: slot m < M holds sa[m] a_m[i], slot M + m holds b_m[i]; split into BF16
+  // high and low parts (K-major canonical image).
   for (int idx = tid; idx < kGtBM * K1; idx += kGtThreads) {
     const int m = idx / kGtBM, il = idx - m * kGtBM;
     const long long i = row0 + il;
-    const float v = (m < a.M && i < a.n) ? a.sa[m] * a.A[(long long)a.amap[m] * a.ld + i] : 0.f;
+    float v = 0.f;
+    if (i < a.n) {
+      if (m < a.M) v = a.sa[m] * a.A[(long long)a.amap[m] * a.ld + i];
+      else if (m < 2 * a.M) v = a.B[(long long)a.bmap[m - a.M] * a.ld + i];
+    }
     __nv_bfloat16 h, l;
     split_bf16(v, h, l);
     const uint32_t off = tc::canon_offset(il, m, 2, K1 / 8);
@@ -290,7 +319,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
         }
       }
       if (!ok) *s_fail = 1;
-      tc::commit(done);
+      if (nt > 0) tc::commit(done);   // a CTA with an empty range issues nothing and waits on nothing
     }
   } else {
     // ------------- epilogue: 8 warps, (lane quadrant, column half) each -------------
@@ -315,6 +344,10 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
       const uint32_t wcol = tbase + lane_base + (uint32_t)(b * 32 + half * 16);
       float w[16];
       tc::tmem_ld16(wcol, w);
+      if (tile_begin + lt < diag_end) {   // a tile of I itself: (i, j) and (j, i) both visited
+#pragma unroll
+        for (int q = 0; q < 16; ++q) w[q] *= 0.5f;
+      }
       const float* tx = reinterpret_cast<const float*>(stage(s));
       const float* tb = reinterpret_cast<const float*>(stage(s) + S::X_BYTES);
       uint32_t hi[8], lo[8];
@@ -349,7 +382,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
       if (lane == 0) tc::mbar_arrive(&p_full[b]);
     }
     if (!ok) *s_fail = 1;
-    const bool fin = ok && gt_warp_wait(done, 0);
+    const bool fin = ok && (nt == 0 || gt_warp_wait(done, 0));
     ok = __all_sync(0xffffffffu, fin && !*s_fail);
     if (ok && nt > 0) {
       tc::fence_after();
@@ -384,7 +417,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
 
   // -------- all roles: release tensor memory; CTA reduction; last CTA sums the partials -------
   if (warp == 1) {
-    if (lane == 0) (void)mbar_wait_spin(done, 0);
+    if (lane == 0 && nt > 0) (void)mbar_wait_spin(done, 0);
     __syncwarp();
   }
   tc::fence_before();
@@ -432,18 +465,21 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   if (tid == 0) *a.counter = 0;
 }
 
-// Split of the j range: every SM works through its share of the (row block, split) items in
-// turn, so the pass takes about ceil(items / SMs) x (tiles per item + a fixed cost per item:
-// the A^ image, the pipeline fill and the reduction, about six tiles' worth).
-static int plan_gt_split(long long n_rb, long long ntiles, int num_sms) {
-  long long best = -1;
+// Split of each row block's tile range into s CTAs.  The SMs share the visited tiles plus a
+// fixed cost per CTA (the operand image, the pipeline fill and the reduction, about six
+// tiles' worth); a CTA shares its SM with occ - 1 others, so the longest range (row block 0,
+// ntiles / s tiles) takes about occ x its length and must not end the pass.
+static int plan_gt_split(long long n_rb, long long ntiles, int num_sms, int occ) {
+  const long long per_block = kGtBM / kGtBN;
+  const long long visited = n_rb * ntiles - per_block * n_rb * (n_rb - 1) / 2;
   // no more than kTcMaxSplitTiles tiles per CTA: the sums accumulate in FP32 in tensor memory
   const int s_min = (int)((ntiles + kTcMaxSplitTiles - 1) / kTcMaxSplitTiles);
+  long long best = -1;
   int best_s = s_min;
   for (int s = s_min; s <= std::max(64, s_min) && s <= ntiles; ++s) {
-    const long long items = n_rb * s;
-    const long long per = (ntiles + s - 1) / s;
-    const long long cost = (items + num_sms - 1) / num_sms * (per + 6);
+    const long long shared = (visited + 6 * n_rb * s + num_sms - 1) / num_sms;
+    const long long longest = ((ntiles + s - 1) / s + 6) * occ;
+    const long long cost = std::max(shared, longest);
     if (best < 0 || cost < best) {
       best = cost;
       best_s = s;
@@ -473,12 +509,10 @@ struct GtInst {
     return occ;
   }
   static cudaError_t launch(GradLaunch& L, cudaStream_t s) {
-    (void)occupancy();
+    const int occ = occupancy();
     const long long ntiles = (L.n + kGtBN - 1) / kGtBN;
     const int n_rb = (int)((L.n + kGtBM - 1) / kGtBM);
-    const int s_plan = plan_gt_split(n_rb, ntiles, L.num_sms);
-    const int tiles_per_split = (int)((ntiles + s_plan - 1) / s_plan);
-    const int nsplit = (int)((ntiles + tiles_per_split - 1) / tiles_per_split);
+    const int nsplit = plan_gt_split(n_rb, ntiles, L.num_sms, occ);
     const size_t need = (size_t)n_rb * nsplit * kMaxP;
     if (L.plan_only) {
       L.need_partials_len = need;
@@ -494,8 +528,10 @@ struct GtInst {
     {
       const long long total = ntiles * kGtBN * S::K1;
       const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * L.num_sms);
-      pack_bt_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.B), L.ld, L.bmap, L.M,
-                                            S::K1, L.n, ntiles, hi, lo);
+      pack_bt_kernel<<<blocks, 256, 0, s>>>(static_cast<const float*>(L.B), L.bmap,
+                                            static_cast<const float*>(L.A), L.amap,
+                                            static_cast<const float*>(L.sa), L.ld, L.M, S::K1,
+                                            L.n, ntiles, hi, lo);
     }
     {
       const long long total = ntiles * S::N2 * kGtBN;
@@ -521,7 +557,6 @@ struct GtInst {
     a.d = L.d;
     a.params = L.params;
     a.nsplit = nsplit;
-    a.tiles_per_split = tiles_per_split;
     a.ntiles = (int)ntiles;
     a.partials = L.partials;
     a.counter = L.counter;
@@ -532,11 +567,14 @@ struct GtInst {
   }
 };
 
+// KS = 16-wide steps of the 2M factor slots.
 template <int DP>
 static cudaError_t grad_tc_dispatch_m(GradLaunch& L, cudaStream_t s) {
-  if (L.M <= 16) return GtInst<DP, 1>::launch(L, s);
-  if (L.M <= 32) return GtInst<DP, 2>::launch(L, s);
-  if (L.M <= 64) return GtInst<DP, 4>::launch(L, s);
+  if (L.M <= 8) return GtInst<DP, 1>::launch(L, s);
+  if (L.M <= 16) return GtInst<DP, 2>::launch(L, s);
+  if (L.M <= 24) return GtInst<DP, 3>::launch(L, s);
+  if (L.M <= 32) return GtInst<DP, 4>::launch(L, s);
+  if (L.M <= 64) return GtInst<DP, 8>::launch(L, s);
   return cudaErrorInvalidValue;
 }
 

@@ -13,6 +13,7 @@ constexpr int kBN = 64;          // points per staged j-tile
 constexpr int kStages = 3;       // staged j-tiles in flight per CTA
 constexpr int kMaxRChunk = 32;   // right-hand sides per K V launch
 constexpr int kMaxM = 64;        // rank of the gradient's bilinear form per launch
+constexpr int kGtScratchRows = 128 + 48;   // tensor-core gradient operand scratch (x tc_ld)
 
 // Device status bits (OR-ed into the context's status word).
 constexpr int kStatusBreakdown = 1;
@@ -258,7 +259,8 @@ struct GradLaunch {
   size_t need_partials_len;  // set when partials_len is too small
   bool plan_only;            // only fill need_partials_len (no launch)
   // tensor-core pass (launch_grad_tc) only: row norms (launch_prescale_tc) and BF16 packed
-  // scratch, high and low parts, 112 x tc_ld elements each (tc_ld = n rounded up to 128)
+  // scratch, high and low parts, kGtScratchRows x tc_ld elements each (tc_ld = n rounded up
+  // to 128): the right operand image (2M <= 128 factor slots), then the point features Z
   const float* bneg;
   void* tc_hi;
   void* tc_lo;
