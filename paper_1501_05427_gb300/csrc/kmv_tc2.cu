@@ -1,15 +1,20 @@
 // Mixed-precision tile-generating K V with the cross term on the tensor cores too.
 //
 // For a block of 128 output rows I and a 32-point tile J:
-//   1. C_IJ = A_I B_J^T on the tensor cores (kind::tf32) with the augmented rows
+//   1. C_IJ = A_I B_J^T on the tensor cores (kind::tf32).  With padded d = 2 or 4 the rows
+//      carry the column term too,
 //          A_i = [x^_i, 1],  B_j = [2 c1 x^_j, b_j],   b_j = -c1 |x^_j|^2, c1 = log2(e)/2,
-//      so that C_ij = 2 c1 x^_i . x^_j + b_j (K = d + 1 padded to a multiple of 8); both
-//      sides split into a TF32 high part and the remainder, three products (Ah Bh + Ah Bl +
-//      Al Bh), FP32 accumulation into a 32-column tensor-memory buffer;
+//      so that C_ij = 2 c1 x^_i . x^_j + b_j in one 8-wide K step; with padded d = 8 or 16
+//      the rows are A_i = x^_i, B_j = 2 c1 x^_j (K = d: the augmented column would cost a
+//      whole further K step, three MMAs per tile on the one issuing thread that paces the
+//      kernel) and the epilogue adds b_j.  Both sides split into a TF32 high part and the
+//      remainder, three products (Ah Bh + Ah Bl + Al Bh), FP32 accumulation into a 32-column
+//      tensor-memory buffer;
 //   2. the epilogue warps read C back (tcgen05.ld) and form
-//          k_ij = exp2(a_i + C_ij),   a_i = log2(sigma^2) - c1 |x^_i|^2
-//      (one FADD and one ex2 per entry), split k into BF16 high and low parts and store them
-//      over C's own columns (tcgen05.st);
+//          k_ij = exp2(a_i + C_ij)  or  exp2((a_i + b_j) + C_ij),
+//          a_i = log2(sigma^2) - c1 |x^_i|^2
+//      (one or two FADDs and one ex2 per entry), split k into BF16 high and low parts and
+//      store them over C's own columns (tcgen05.st);
 //   3. U_I += K_IJ V_J on the tensor cores with V split into BF16 high + low parts (three
 //      products), FP32 accumulation in tensor memory, as in the FP32-pipe variant.
 // The TF32 images of A and B (high and low parts, K-major canonical, 32-point tiles back to
@@ -36,9 +41,10 @@ constexpr int kT2BM = 128;
 constexpr int kT2Threads = 320;    // warp 0 producer, warp 1 MMA issuer, warps 2-9 epilogue
 constexpr uint32_t kT2Cols = 128;  // tensor-memory columns per CTA
 
-// The augmented rows A_j = [x^_j, 1, 0...] and B_j = [2 c1 x^_j, b_j, 0...] for j in [0, rows)
-// as TF32 high part and remainder, K8 columns, in 32-row K-major canonical tiles; rows >= n
-// are zero.  b_j = -c1 |x^_j|^2 is read from the row norms of launch_prescale_tc.
+// The rows A_j = [x^_j, 1, 0...] and B_j = [2 c1 x^_j, b_j, 0...] for j in [0, rows) as TF32
+// high part and remainder, K8 columns, in 32-row K-major canonical tiles; rows >= n are zero.
+// When K8 == DP there is no slot for the augmented column (A_j = x^_j, B_j = 2 c1 x^_j).
+// b_j = -c1 |x^_j|^2 is read from the row norms of launch_prescale_tc.
 __global__ void pack_x_tf32_kernel(const float* __restrict__ xhat, const float* __restrict__ bneg,
                                    const DevParams* __restrict__ params, int DP, int K8,
                                    long long n, long long rows, float* __restrict__ Ahi,
@@ -93,12 +99,15 @@ struct Tc2DevArgs {
   int* status;
 };
 
-template <int K8, int N>
+// BJ: the epilogue adds b_j (the rows are not augmented); the stage then carries b_J.
+template <int K8, int N, bool BJ>
 struct Tc2Shape {
   static constexpr uint32_t A_BYTES = kT2BM * K8 * 4;   // one part of the A_I image
   static constexpr uint32_t XB_BYTES = kT2BN * K8 * 4;  // one part of the B_J image
   static constexpr uint32_t V_BYTES = N * kT2BN * 2;    // one part of the BF16 V_J tile
-  static constexpr uint32_t STAGE_BYTES = 2 * XB_BYTES + 2 * V_BYTES;
+  static constexpr uint32_t BN_BYTES = BJ ? kT2BN * 4 : 0;   // b_J
+  static constexpr uint32_t OFF_BN = 2 * XB_BYTES + 2 * V_BYTES;   // within a stage
+  static constexpr uint32_t STAGE_BYTES = 2 * XB_BYTES + 2 * V_BYTES + BN_BYTES;
   // four stages while four CTAs still fit in shared memory (~54 KB each), else three
   static constexpr int ST = (2 * A_BYTES + 4 * STAGE_BYTES <= 54 * 1024) ? 4 : 3;
   static constexpr uint32_t OFF_STAGES = 2 * A_BYTES;
@@ -140,9 +149,9 @@ __device__ inline void t2_ld_cols(uint32_t taddr, float (&v)[NH]) {
   }
 }
 
-template <int K8, int N>
+template <int K8, int N, bool BJ>
 __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs a) {
-  using S = Tc2Shape<K8, N>;
+  using S = Tc2Shape<K8, N, BJ>;
   constexpr int ST = S::ST;
   constexpr int NB = S::NB;
   constexpr int NH = N / 2;
@@ -212,6 +221,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
         unsigned char* sv = st + 2 * S::XB_BYTES;
         bulk_g2s(sv, a.V_hi + t * N * kT2BN, S::V_BYTES, &full[s]);
         bulk_g2s(sv + S::V_BYTES, a.V_lo + t * N * kT2BN, S::V_BYTES, &full[s]);
+        if constexpr (BJ) bulk_g2s(st + S::OFF_BN, a.bneg + t * kT2BN, S::BN_BYTES, &full[s]);
         issued = lt + 1;
       }
     }
@@ -284,9 +294,14 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
     bool ok = true;
     for (int lt = half; lt < nt; lt += 2) {
       const int b = lt % NB;
-      const bool ready = t2_warp_wait(&c_full[lt % S::NCF], (uint32_t)((lt / S::NCF) & 1));
+      // b_J is read from the stage: wait for its copy too (the stage is refilled only after
+      // this tile's contraction, which waits for this warp's K)
+      const bool ready =
+          t2_warp_wait(&c_full[lt % S::NCF], (uint32_t)((lt / S::NCF) & 1)) &&
+          (!BJ || t2_warp_wait(&full[lt % ST], (uint32_t)((lt / ST) & 1)));
       if (!__all_sync(0xffffffffu, ready && !*s_fail)) { ok = false; break; }
       tc::fence_after();
+      const float* bj = reinterpret_cast<const float*>(stage(lt % ST) + S::OFF_BN);
       // all 32 columns of C in one tensor-memory round trip; each pair's K high and low parts
       // are written back into the pair's own registers (no extra registers live)
       const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32);
@@ -295,8 +310,14 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         // the exponent is <= log2 sigma^2 up to rounding (about 1e-6 relative in k)
-        const float k0 = ex2_approx(ai + __uint_as_float(c[2 * q]));
-        const float k1 = ex2_approx(ai + __uint_as_float(c[2 * q + 1]));
+        float e0 = ai, e1 = ai;
+        if constexpr (BJ) {
+          const float2 b2 = *reinterpret_cast<const float2*>(bj + 2 * q);
+          e0 += b2.x;
+          e1 += b2.y;
+        }
+        const float k0 = ex2_approx(e0 + __uint_as_float(c[2 * q]));
+        const float k1 = ex2_approx(e1 + __uint_as_float(c[2 * q + 1]));
         const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
         const float2 hf = __bfloat1622float2(h);
         const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
@@ -388,15 +409,15 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
   if (tid == 0) a.counters[rb] = 0;
 }
 
-template <int K8, int N>
+template <int K8, int N, bool BJ>
 struct Tc2Inst {
-  using S = Tc2Shape<K8, N>;
+  using S = Tc2Shape<K8, N, BJ>;
   // CTAs per SM: shared memory, tensor memory (512 columns) and the launch bound.
   static int occupancy() {
     static int occ = -1;
     static std::once_flag once;
     std::call_once(once, [] {
-      auto fn = kmv_tc2_kernel<K8, N>;
+      auto fn = kmv_tc2_kernel<K8, N, BJ>;
       cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::SMEM);
       cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       int dev = 0, smem_sm = 0;
@@ -452,29 +473,32 @@ struct Tc2Inst {
     a.status = L.status;
     (void)occupancy();
     const int nrb = (int)((L.n + kT2BM - 1) / kT2BM);
-    kmv_tc2_kernel<K8, N><<<nrb * a.nsplit, kT2Threads, S::SMEM, s>>>(a);
+    kmv_tc2_kernel<K8, N, BJ><<<nrb * a.nsplit, kT2Threads, S::SMEM, s>>>(a);
     return cudaGetLastError();
   }
 };
 
-template <int K8>
+template <int K8, bool BJ>
 static cudaError_t tc2_dispatch_n(TcLaunch& L, cudaStream_t s) {
   const int r = std::max(L.R, L.n_min);
-  if (r <= 16) return Tc2Inst<K8, 16>::launch(L, s);
-  if (r <= 32) return Tc2Inst<K8, 32>::launch(L, s);
-  if (r <= 64) return Tc2Inst<K8, 64>::launch(L, s);
+  if (r <= 16) return Tc2Inst<K8, 16, BJ>::launch(L, s);
+  if (r <= 32) return Tc2Inst<K8, 32, BJ>::launch(L, s);
+  if (r <= 64) return Tc2Inst<K8, 64, BJ>::launch(L, s);
   return cudaErrorInvalidValue;
 }
 
-// K8 = d + 1 rounded up to a multiple of 8 (the TF32 MMA's K), from the padded d.
-static int tc2_k8(int DP) { return (DP + 1 + 7) / 8 * 8; }
+// K8, the TF32 MMA's K (a multiple of 8), from the padded d: padded d 2 and 4 take the
+// augmented column within one K step (K8 = 8); padded d 8 and 16 leave it to the epilogue
+// (K8 = d).
+static int tc2_k8(int DP) { return DP >= 8 ? DP : 8; }
 
 cudaError_t launch_kmv_tc2(TcLaunch& L, cudaStream_t s) {
   if (L.R < 1 || L.R > 64 || !L.X_hi || !L.X_lo) return cudaErrorInvalidValue;
-  switch (tc2_k8(L.DP)) {
-    case 8: return tc2_dispatch_n<8>(L, s);
-    case 16: return tc2_dispatch_n<16>(L, s);
-    case 24: return tc2_dispatch_n<24>(L, s);
+  switch (L.DP) {
+    case 2:
+    case 4: return tc2_dispatch_n<8, false>(L, s);
+    case 8: return tc2_dispatch_n<8, true>(L, s);
+    case 16: return tc2_dispatch_n<16, true>(L, s);
     default: return cudaErrorInvalidValue;
   }
 }
