@@ -126,6 +126,8 @@ def parse_args():
                          "K V, uneven batch, 2-D FP64 chain)")
     ap.add_argument("--c3-rows", type=int, default=4000,
                     help="output rows of the near-duplicate K V the oracle evaluates")
+    ap.add_argument("--c5-steps", type=int, default=1000,
+                    help="steps of the learned warm start's recording trajectory (0: skip)")
     ap.add_argument("--grad-reps", type=int, default=100,
                     help="repetitions of the gradient-error measurement")
     return ap.parse_args()
@@ -444,25 +446,26 @@ def _exact_gradient_torch(X, y, psi, dev):
     return np.array(g)
 
 
-def grad_error_leg(dev, stream, reps):
+def grad_error_leg(dev, stream, reps, prob=None):
     """Sec. 5's gradient error ||g - g~||^2 / ||g||^2 over `reps` seeded repetitions on a
-    Census-shaped problem small enough for a dense Cholesky (n = 4,000, 16 probes), at the
-    generating parameters + 0.3 (where ||g|| is not ~0).  Paths: plain FP32 (probes redrawn
-    every step, cold solves), mixed (tensor cores, same options) and the chosen form (mixed,
-    probes reused for 20 steps, warm-started solves); same seeds on every path."""
+    problem small enough for a dense Cholesky (default: Census-shaped, n = 4,000; 16 probes),
+    at the generating parameters + 0.3 (where ||g|| is not ~0).  Paths: plain FP32 (probes
+    redrawn every step, cold solves), mixed (tensor cores, same options) and the chosen form
+    (mixed, probes reused for 20 steps, warm-started solves); same seeds on every path."""
     import torch
 
     from paper_1501_05427_gb300 import ulisse as u
     from paper_1501_05427_gb300 import workloads as w
-    prob = w.census_like(n=4000, seed=20150124)
+    prob = prob if prob is not None else w.census_like(n=4000, seed=20150124)
     psi = prob.psi_true + 0.3
     t0 = time.perf_counter()
     g = _exact_gradient_torch(prob.X, prob.y, psi, dev)
     t_exact = time.perf_counter() - t0
     X = torch.from_numpy(prob.X).to(dev)
     y = torch.from_numpy(prob.y).to(dev)
-    out = {"statistic": "||g - g~||^2 / ||g||^2 over %d seeded repetitions, census_like "
-                        "n=4000, 16 probes, q=1, psi = truth + 0.3" % reps,
+    out = {"statistic": "||g - g~||^2 / ||g||^2 over %d seeded repetitions, %s "
+                        "n=%d, d=%d, 16 probes, q=1, psi = truth + 0.3"
+                        % (reps, prob.name, prob.n, prob.d),
            "g_norm": float(np.linalg.norm(g)),
            "reference": "dense FP64 Cholesky on the device (%.1f s)" % t_exact}
     legs = (("plain_fp32", u.PREC_FP32, 1, 0), ("mixed", u.PREC_MIXED, 1, 0),
@@ -491,6 +494,159 @@ def grad_error_leg(dev, stream, reps):
     out["rounds_at_equal_error_plain_over"] = {
         k: {"median": base["median_x_rounds"] / out[k]["median_x_rounds"],
             "p90": base["p90_x_rounds"] / out[k]["p90_x_rounds"]} for k in ("mixed", "chosen")}
+    return out
+
+
+def near_duplicates_subproblem_leg(dev, stream, reps):
+    """The near-duplicate inputs (d = 16, 1% jittered copies) at n = 4,000, where a dense FP64
+    Cholesky gives the exact values: the error of a converged solve K^{-1} y (q = 0) per path
+    against the Cholesky solution, and the gradient-error statistic of grad_error_leg."""
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+    prob = w.near_duplicates(n=4000)
+    psi = prob.psi_true + 0.3
+    Xd = torch.from_numpy(prob.X).to(dev, torch.float64)
+    yd = torch.from_numpy(prob.y).to(dev, torch.float64)
+    ell = torch.tensor(psi[:prob.d], dtype=torch.float64, device=dev).exp()
+    s2, lam = math.exp(psi[prob.d]), math.exp(psi[prob.d + 1])
+    Xs = Xd / ell
+    K = s2 * torch.exp(-0.5 * torch.cdist(Xs, Xs) ** 2) + lam * torch.eye(prob.n, device=dev,
+                                                                           dtype=torch.float64)
+    s_exact = torch.linalg.solve(K, yd)
+    cond = float(torch.linalg.cond(K))
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    out = {"workload": "near_duplicates", "n": prob.n, "d": prob.d,
+           "duplicates": int(prob.meta["duplicates"]), "cond_K": cond, "solve": {}}
+    for name, prec in (("fp32", u.PREC_FP32), ("mixed", u.PREC_MIXED)):
+        cfg = u.ulisse_config_default(precision=prec, q=0.0, eps=1e-3, max_iter=5000)
+        with u.Context(X, y, cfg, stream=stream) as ctx:
+            S, st = ctx.solve(psi, y[:, None], allow=(u.ULISSE_ERR_MAXITER,))
+        sv = S[:, 0].double()
+        out["solve"][name] = {
+            "iterations": int(st[0][1]),
+            "rel_error_vs_cholesky": float(torch.linalg.norm(sv - s_exact) /
+                                           torch.linalg.norm(s_exact)),
+            "rel_residual": float(torch.linalg.norm(yd - K @ sv) / torch.linalg.norm(yd))}
+    out["solve"]["stopping_rule"] = ("||y - K s|| < 1e-3 (FP32 vectors); the solution error "
+                                     "is bounded by that residual / lambda_min(K)")
+    out["gradient_error"] = grad_error_leg(dev, stream, reps, prob)
+    return out
+
+
+def learned_warm_start_leg(dev, stream, rec_steps=1000, rec_every=4, n_eval=16, var_cols=8,
+                           var_calls=3):
+    """The learned warm start x0 = K_s(X, Z) c, c = MLP(psi), at the workload it is meant for
+    (n = 100,000, d = 8, 16 probes, noise variance 0.05): pairs are recorded along the first
+    `rec_steps` steps of a parameter trajectory (every `rec_every`-th step, at most 256 pairs),
+    the network is trained on them, and on held-out parameters the y solve (q = 1, two
+    estimators) is run from x0 = 0, from the pooled constant c (the network's starting point)
+    and from the trained network: CG iterations (= K V products) of each, and the variance of
+    the y term 1/2 s1^T dK s2 of the gradient with and without the learned start.
+
+    The trajectory is a seeded AR(1) walk around the generating parameters (stationary s.d.
+    0.046 per coordinate), a stand-in for the chain's states: a free-running chain at a
+    constant step size is thrown by the heavy-tailed gradient estimates (see the chain
+    test), and the walk gives the network the same kind of parameter spread to learn from."""
+    import torch
+
+    from paper_1501_05427_gb300 import ulisse as u
+    from paper_1501_05427_gb300 import workloads as w
+    prob = w.warm_start_problem()
+    n, p = prob.n, prob.d + 2
+    rng = np.random.default_rng(20150105)
+    walk, z = [], np.zeros(p)
+    for _ in range(rec_steps + rec_every * n_eval):
+        z = 0.9 * z + 0.02 * rng.standard_normal(p)
+        walk.append(prob.psi_true + z)
+    X = torch.from_numpy(prob.X).to(dev)
+    y = torch.from_numpy(prob.y).to(dev)
+    cfg = u.ulisse_config_default(precision=u.PREC_MIXED, n_probes=16, probe_refresh=20,
+                                  warm_start_probes=1, seed=55, max_iter=3000)
+    allow = (u.ULISSE_ERR_MAXITER,)
+    out = {"workload": "warm_start (census_like shape)", "n": n, "d": prob.d, "n_probes": 16,
+           "network": "MLP %d -> 256 -> 256 -> 512 (tanh), 512 anchors, FP32 training, BF16 "
+                      "inference" % p,
+           "trajectory": "AR(1) walk around the generating parameters, s.d. 0.046",
+           "recorded": "%d pairs from the first %d steps (every %d-th)"
+                       % (min(256, rec_steps // rec_every), rec_steps, rec_every)}
+    with u.Context(X, y, cfg, stream=stream) as ctx:
+        ctx.ws_init(n_anchors=512, hidden=256, n_rows=1024, max_pairs=256, seed=1)
+        # a recorded pair (psi_t, rows, y_rows, K(X_rows, X) K_s(X, Z)) does not depend on the
+        # step's solves, so only the recorded steps are run (plus a few plain ones, timed for
+        # the recording's cost)
+        t_rec = t_plain = 0.0
+        n_rec = n_plain = 0
+        for t in range(rec_steps):
+            rec = (t % rec_every == 0)
+            if not rec and n_plain >= 20:
+                continue
+            ctx.ws_set(record=rec, use=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.grad(walk[t], step=t, allow=allow)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if rec:
+                t_rec += dt
+                n_rec += 1
+            else:
+                t_plain += dt
+                n_plain += 1
+        out["step_ms_recording"] = 1e3 * t_rec / max(n_rec, 1)
+        out["step_ms_not_recording"] = 1e3 * t_plain / max(n_plain, 1)
+        ctx.ws_set(record=False, use=False)
+        held = [walk[rec_steps + rec_every * k] for k in range(n_eval)]
+        # held-out loss of the pooled constant: one Adam step of negligible size, validated
+        # against the pooled start it begins from
+        out["pooled_heldout_loss"] = ctx.ws_train(steps=1, batch=64, lr=1e-12)
+        ctx.ws_train(steps=0, batch=64)
+        x_pool = [ctx.ws_x0(ps, bf16=True).clone() for ps in held]
+        t0 = time.perf_counter()
+        loss = ctx.ws_train(steps=600, batch=64, lr=2e-3)
+        out["training_s"] = time.perf_counter() - t0
+        out["training_heldout_loss"] = loss
+        x_net = [ctx.ws_x0(ps, bf16=True).clone() for ps in held]
+        its = {"x0_zero": [], "pooled_constant": [], "network": []}
+        for k, ps in enumerate(held):
+            for name, s0 in (("x0_zero", None), ("pooled_constant", x_pool[k][:, None]),
+                             ("network", x_net[k][:, None])):
+                _, st = ctx.solve(ps, y[:, None], n_est=[2], S0=s0, step=50_000 + k,
+                                  allow=allow)
+                its[name].append(int(st[0][1]))
+        out["y_solve_iterations_heldout"] = {
+            k: {"mean": float(np.mean(v)), "median": float(np.median(v))} for k, v in its.items()}
+        out["kv_products_saved_vs_x0_zero"] = {
+            k: 1.0 - float(np.mean(its[k])) / float(np.mean(its["x0_zero"]))
+            for k in ("pooled_constant", "network")}
+        # variance of the y term of the gradient at one held-out point: var_cols columns of y
+        # per call (independent truncation draws per column), var_calls calls
+        ps = held[0]
+        B = y[:, None].repeat(1, var_cols)
+        terms = {"x0_zero": [], "pooled_constant": [], "network": []}
+        iters = {"x0_zero": [], "pooled_constant": [], "network": []}
+        for name, s0 in (("x0_zero", None),
+                         ("pooled_constant", x_pool[0][:, None].repeat(1, var_cols)),
+                         ("network", x_net[0][:, None].repeat(1, var_cols))):
+            for c in range(var_calls):
+                S, st = ctx.solve(ps, B, n_est=[2] * var_cols, S0=s0, step=60_000 + c,
+                                  allow=allow)
+                iters[name] += [int(e[1]) for e in st]
+                for j in range(var_cols):
+                    terms[name].append(ctx.dk_bilinear(ps, S[:, 2 * j:2 * j + 1],
+                                                       S[:, 2 * j + 1:2 * j + 2], [0.5]))
+        var = {k: float(np.var(np.array(v), axis=0, ddof=1).sum()) for k, v in terms.items()}
+        it = {k: float(np.mean(v)) for k, v in iters.items()}
+        out["y_term_gradient_variance"] = {
+            "samples": var_cols * var_calls,
+            "trace": var, "iterations": it,
+            "variance_ratio_over_x0_zero": {k: var[k] / var["x0_zero"]
+                                            for k in ("pooled_constant", "network")},
+            "variance_x_iterations_ratio_over_x0_zero": {
+                k: var[k] * it[k] / (var["x0_zero"] * it["x0_zero"])
+                for k in ("pooled_constant", "network")}}
     return out
 
 
@@ -853,6 +1009,10 @@ def run_ours(args):
     if world == 1 and not args.no_extras:
         extras["gradient_error"] = grad_error_leg(dev, stream, args.grad_reps)
         extras["near_duplicates_kv"] = near_duplicates_leg(dev, stream, flush, args.c3_rows)
+        extras["near_duplicates_subproblem"] = near_duplicates_subproblem_leg(
+            dev, stream, max(10, args.grad_reps // 2))
+        if args.c5_steps > 0:
+            extras["learned_warm_start"] = learned_warm_start_leg(dev, stream, args.c5_steps)
         extras["uneven_batch"] = uneven_batch_leg(args, dev, stream, flush)
         extras["small_2d_fp64_chain"] = small_2d_leg(dev, stream)
         extras["pcg"] = pcg_leg(dev, stream, flush, X, y, prob.psi_true)
@@ -882,6 +1042,8 @@ def run_ours(args):
                       for path, tab in tuned.items()} if tuned else None),
         "gradient_error": extras.get("gradient_error"),
         "near_duplicates_kv": extras.get("near_duplicates_kv"),
+        "near_duplicates_subproblem": extras.get("near_duplicates_subproblem"),
+        "learned_warm_start": extras.get("learned_warm_start"),
         "uneven_batch": extras.get("uneven_batch"),
         "small_2d_fp64_chain": extras.get("small_2d_fp64_chain"),
         "pcg": extras.get("pcg"),
