@@ -351,23 +351,30 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
       const float* tx = reinterpret_cast<const float*>(stage(s));
       const float* tb = reinterpret_cast<const float*>(stage(s) + S::X_BYTES);
       uint32_t hi[8], lo[8];
+      // packed FP32x2 instructions: the cross term two coordinates at a time, the weight and
+      // the high/low split two entries at a time
+      const float2 minus1 = make_float2(-1.f, -1.f);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
-        float pk[2];
+        float ex[2];
         const float2 bj = *reinterpret_cast<const float2*>(tb + half * 16 + 2 * q);
 #pragma unroll
         for (int h2 = 0; h2 < 2; ++h2) {
           const int j = half * 16 + 2 * q + h2;
           float xj[DP];
           load_row<float, DP>(tx + j * DP, xj);
-          float ex = ai + (h2 == 0 ? bj.x : bj.y);
+          float2 acc = make_float2(ai + (h2 == 0 ? bj.x : bj.y), 0.f);
 #pragma unroll
-          for (int k = 0; k < DP; ++k) ex = fmaf(xi[k], xj[k], ex);
-          pk[h2] = ex2_approx(fminf(ex, c0)) * w[2 * q + h2];
+          for (int k = 0; k < DP; k += 2)
+            acc = __ffma2_rn(make_float2(xi[k], xi[k + 1]), make_float2(xj[k], xj[k + 1]), acc);
+          ex[h2] = acc.x + acc.y;
         }
-        const __nv_bfloat162 h = __floats2bfloat162_rn(pk[0], pk[1]);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(pk[0] - hf.x, pk[1] - hf.y);
+        const float2 pk = __fmul2_rn(make_float2(ex2_approx(fminf(ex[0], c0)),
+                                                 ex2_approx(fminf(ex[1], c0))),
+                                     make_float2(w[2 * q], w[2 * q + 1]));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(pk.x, pk.y);
+        const float2 r = __ffma2_rn(__bfloat1622float2(h), minus1, pk);   // pk - high part
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
         hi[q] = *reinterpret_cast<const uint32_t*>(&h);
         lo[q] = *reinterpret_cast<const uint32_t*>(&l);
       }

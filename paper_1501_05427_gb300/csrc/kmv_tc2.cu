@@ -307,20 +307,20 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
       const uint32_t ccol = tbase + lane_base + (uint32_t)(b * 32);
       uint32_t c[32];
       tc::tmem_ld16x2(ccol, c);
+      // two entries per packed FP32x2 instruction (FADD2 / FFMA2, the same rounding as the
+      // scalar forms)
+      const float2 ai2 = make_float2(ai, ai);
+      const float2 minus1 = make_float2(-1.f, -1.f);
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         // the exponent is <= log2 sigma^2 up to rounding (about 1e-6 relative in k)
-        float e0 = ai, e1 = ai;
-        if constexpr (BJ) {
-          const float2 b2 = *reinterpret_cast<const float2*>(bj + 2 * q);
-          e0 += b2.x;
-          e1 += b2.y;
-        }
-        const float k0 = ex2_approx(e0 + __uint_as_float(c[2 * q]));
-        const float k1 = ex2_approx(e1 + __uint_as_float(c[2 * q + 1]));
-        const __nv_bfloat162 h = __floats2bfloat162_rn(k0, k1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(k0 - hf.x, k1 - hf.y);
+        float2 e = ai2;
+        if constexpr (BJ) e = __fadd2_rn(e, *reinterpret_cast<const float2*>(bj + 2 * q));
+        e = __fadd2_rn(e, make_float2(__uint_as_float(c[2 * q]), __uint_as_float(c[2 * q + 1])));
+        const float2 k = make_float2(ex2_approx(e.x), ex2_approx(e.y));
+        const __nv_bfloat162 h = __floats2bfloat162_rn(k.x, k.y);
+        const float2 r = __ffma2_rn(__bfloat1622float2(h), minus1, k);   // k - high part
+        const __nv_bfloat162 l = __floats2bfloat162_rn(r.x, r.y);
         c[2 * q] = *reinterpret_cast<const uint32_t*>(&h);
         c[2 * q + 1] = *reinterpret_cast<const uint32_t*>(&l);
       }
