@@ -504,6 +504,22 @@ typedef struct {
 ulisse_status ulisse_autotune(ulisse_ctx *ctx, const double *psi, int max_cols, int reps,
                               ulisse_tune_entry *out);
 
+/* Install a K V launch table, e.g. one that ulisse_autotune returned in an earlier run on the
+ * same device and problem size, so that a new context skips the tuning (the paper has no
+ * counterpart).  table: host, n entries (1 <= n <= 32); entry k is used for products of
+ * k + 1 columns.  Per entry (live_cols, ms and ms_default are ignored):
+ *   width: k + 1 .. 64; the smallest compiled column count at least this wide is used
+ *          (tensor cores: the MMA N 16, 32 or 64; SIMT: up to 32);
+ *   rows_per_thread: SIMT 2 or 4 (ignored on the tensor-core path);
+ *   nsplit: 0 (the launch plan's choice) or 1 .. 64 (the j range is still split further
+ *           where a tensor-core CTA would exceed its accumulation bound);
+ *   cross_term: tensor-core path 1 or 2, SIMT path 0.
+ * Column counts beyond n keep the untuned choice.  Results differ from another table's only
+ * in the summation order of the split j range.  n = 0 (table may be NULL) clears the table.
+ * Errors: ULISSE_ERR_ARG (FP64 or batched context, n out of range, an invalid entry; the
+ * table in use is then unchanged). */
+ulisse_status ulisse_set_tune(ulisse_ctx *ctx, const ulisse_tune_entry *table, int n);
+
 /*
  * Self-test of the failure path (no GPU fault is involved): one CTA waits on an mbarrier
  * that nothing completes.  The wait gives up after about half a second (2^30 SM cycles), the

@@ -2703,6 +2703,30 @@ ulisse_status ulisse_autotune(ulisse_ctx* ctx, const double* psi, int max_cols, 
   return ULISSE_OK;
 }
 
+ulisse_status ulisse_set_tune(ulisse_ctx* ctx, const ulisse_tune_entry* table, int n) {
+  if (!ctx) return ULISSE_ERR_ARG;
+  if (ctx->batched) return fail(ctx, ULISSE_ERR_ARG, "batched context: no K V table");
+  if (ctx->f64) return fail(ctx, ULISSE_ERR_ARG, "the K V table covers the FP32 and mixed paths");
+  if (n < 0 || n > kMaxRChunk || (n > 0 && !table))
+    return fail(ctx, ULISSE_ERR_ARG, "n must be 0..32 (and the table non-null)");
+  std::vector<ulisse_ctx::KmvTune> t((size_t)n);
+  for (int k = 0; k < n; ++k) {
+    const ulisse_tune_entry& e = table[k];
+    const int nl = k + 1;
+    bool ok = e.width >= nl && e.width <= 64 && e.nsplit >= 0 && e.nsplit <= 64;
+    if (ctx->mixed)
+      ok = ok && (e.cross_term == kCrossPipe || e.cross_term == kCrossTensor);
+    else
+      ok = ok && (e.rows_per_thread == 2 || e.rows_per_thread == 4) && e.cross_term == 0;
+    if (!ok) return fail(ctx, ULISSE_ERR_ARG, "invalid K V table entry " + std::to_string(k));
+    t[k] = ulisse_ctx::KmvTune{e.width, e.rows_per_thread, e.nsplit, e.ms, e.ms_default,
+                               e.cross_term};
+  }
+  ctx->tune = t;
+  ctx->graph_key = -1;   // a captured step graph holds the old configuration
+  return ULISSE_OK;
+}
+
 // One CTA waits on an mbarrier that expects two arrivals and gets one: the wait, bounded by
 // the SM clock here (2^30 cycles, about half a second), runs out and the timeout is recorded
 // in the status word as every kernel records it.

@@ -34,7 +34,7 @@ EXPORTED = [
     "ulisse_destroy", "ulisse_kmv_noalloc", "ulisse_kmv_noalloc_status", "ulisse_ws_init", "ulisse_ws_set", "ulisse_ws_train",
     "ulisse_ws_loss_grad", "ulisse_ws_export", "ulisse_ws_x0", "ulisse_create_batched",
     "ulisse_batch_size", "ulisse_batch_kmv", "ulisse_batch_grad", "ulisse_batch_sgld_step",
-    "ulisse_set_graph", "ulisse_autotune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
+    "ulisse_set_graph", "ulisse_autotune", "ulisse_set_tune", "ulisse_batch_sgld_chain", "ulisse_dk_bilinear",
     "ulisse_selftest_wait_timeout", "ulisse_measure_ex2_rate", "ulisse_predict",
 ]
 
@@ -146,6 +146,7 @@ def load():
     lib.ulisse_batch_sgld_chain.argtypes = [P, P, P, I, U64, P]
     lib.ulisse_set_graph.argtypes = [P, I]
     lib.ulisse_autotune.argtypes = [P, P, I, I, ctypes.POINTER(ulisse_tune_entry)]
+    lib.ulisse_set_tune.argtypes = [P, ctypes.POINTER(ulisse_tune_entry), I]
     lib.ulisse_last_error.argtypes = [P]
     lib.ulisse_last_error.restype = ctypes.c_char_p
     lib.ulisse_destroy.argtypes = [P]
@@ -390,6 +391,16 @@ class Context:
         psi = _f64_host(psi, self.p)
         self._check(self._lib.ulisse_autotune(self._h, _hptr(psi), max_cols, reps, out))
         return [{k: getattr(e, k) for k, _ in ulisse_tune_entry._fields_} for e in out]
+
+    def set_tune(self, table):
+        """Install a K V launch table (a list of dicts as autotune returns, entry k for k + 1
+        columns); an empty list clears it."""
+        arr = (ulisse_tune_entry * max(1, len(table)))()
+        for k, e in enumerate(table):
+            arr[k] = ulisse_tune_entry(k + 1, e["width"], e["rows_per_thread"], e["nsplit"],
+                                       e.get("ms", 0.0), e.get("ms_default", 0.0),
+                                       e["cross_term"])
+        self._check(self._lib.ulisse_set_tune(self._h, arr, len(table)))
 
     def selftest_wait_timeout(self):
         """Run the failure-path self-test; returns the status code (ULISSE_ERR_TIMEOUT)."""

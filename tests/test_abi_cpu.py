@@ -94,6 +94,7 @@ def test_null_pointers_rejected(lib):
     assert lib.ulisse_grad(None, None, 0, None, None) == ulisse.ULISSE_ERR_ARG
     assert lib.ulisse_dk_bilinear(None, None, None, None, 1, None, None) == ulisse.ULISSE_ERR_ARG
     assert lib.ulisse_kmv_noalloc_status(None, None) == ulisse.ULISSE_ERR_ARG
+    assert lib.ulisse_set_tune(None, None, 0) == ulisse.ULISSE_ERR_ARG
     lib.ulisse_destroy(None)
 
 
