@@ -1038,7 +1038,9 @@ def run_ours(args):
         "fp32_same_method": same_method,
         "autotune": ({path: {"tuned_over_untuned_ms": [round(e["ms"] / e["ms_default"], 3)
                                                       for e in tab],
-                             "cross_term": [e["cross_term"] for e in tab]}
+                             "cross_term": [e["cross_term"] for e in tab],
+                             "width": [e["width"] for e in tab],
+                             "nsplit": [e["nsplit"] for e in tab]}
                       for path, tab in tuned.items()} if tuned else None),
         "gradient_error": extras.get("gradient_error"),
         "near_duplicates_kv": extras.get("near_duplicates_kv"),
