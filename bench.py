@@ -826,8 +826,14 @@ def pcg_leg(dev, stream, flush, X, y, psi0, steps=6, warm=2):
 
 
 def uneven_batch_leg(args, dev, stream, flush, K=5, W=2):
-    """The 64-problem uneven batch, one graph launch per batched step (see run_batch)."""
-    return _batch_measure(args, dev, stream, flush, K, W, sampler=None)
+    """The 64-problem uneven batch, one graph launch per batched step (see run_batch): the
+    chosen path's line, with the other precision's measurement beside it."""
+    line = _batch_measure(args, dev, stream, flush, K, W, sampler=None)
+    other = "fp32" if args.path == "mixed" else "mixed"
+    o = _batch_measure(args, dev, stream, flush, K, W, sampler=None, path=other)
+    line[other] = {k: o[k] for k in ("value", "ms_per_step", "mvp_rounds_per_step", "dtype",
+                                      "steps_with_a_column_cut_at_max_iter")}
+    return line
 
 
 def run_ours(args):
@@ -1082,9 +1088,11 @@ def run_ours(args):
     return 0
 
 
-def _batch_measure(args, dev, stream, flush, K, W, sampler=None, world=1, rank=0):
+def _batch_measure(args, dev, stream, flush, K, W, sampler=None, world=1, rank=0, path=None):
     """The 64-problem uneven workload: one batched SGLD step of all problems per graph launch
-    (persistent K V and gradient launches over all problems).  Returns the measurement."""
+    (mixed: every CG round's K V of all problems on the tensor cores in one launch; FP32: one
+    persistent K V launch; the gradient sweep in one persistent FP32 launch).  Returns the
+    measurement."""
     import torch
 
     from paper_1501_05427_gb300 import ulisse as u
@@ -1093,7 +1101,10 @@ def _batch_measure(args, dev, stream, flush, K, W, sampler=None, world=1, rank=0
     # the slowest of 576 columns decides a batched step's rounds; a column that has not
     # stopped after max_iter CG iterations is cut off (reported, not fatal)
     warm = not args.no_warm
-    cfg = u.ulisse_config_default(n_probes=8, probe_kind=u.PROBE_RADEMACHER, q=1.0, beta=1.0,
+    path = path or args.path
+    prec = u.PREC_MIXED if path == "mixed" else u.PREC_FP32
+    cfg = u.ulisse_config_default(precision=prec, n_probes=8, probe_kind=u.PROBE_RADEMACHER,
+                                  q=1.0, beta=1.0,
                                   eps=1e-8, max_iter=3000, seed=20150126 + 1000 * rank,
                                   probe_refresh=args.refresh, warm_start_probes=int(warm))
     allow = (u.ULISSE_ERR_MAXITER,)
@@ -1136,8 +1147,10 @@ def _batch_measure(args, dev, stream, flush, K, W, sampler=None, world=1, rank=0
         "metric": "SGLD steps/s", "value": world * K * len(probs) / (total_ms / 1000.0),
         "unit": "problem-steps/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "bf16x3/f32" if path == "mixed" else "f32",
+        "data": "synthetic",
         "config": {"workload": "uneven_batch", "problems": len(probs), "n_total": n_sum,
+                   "path": path,
                    "n_min": min(p.n for p in probs), "n_max": max(p.n for p in probs),
                    "dims": sorted(set(p.d for p in probs)), "n_probes": 8,
                    "step_form": "host loop" if args.no_graph else "one CUDA graph launch per batched step",

@@ -137,6 +137,15 @@ struct ulisse_ctx {
   double* b_psi = nullptr;         // device: packed parameters of all problems
   int b_np = 0;                    // packed parameter count
   int b_maxch = 1;                 // largest chunk count of the batched CG launches
+  // mixed-precision batches: the tensor-core K V over (problem, 128-row block, split) items
+  bool tc_no_aug = false;          // sub-context of a mixed batch: rows packed without b_j
+  int4* b_tc_items = nullptr;
+  int b_tc_n_items = 0;
+  void* b_tc_args = nullptr;       // 3 x problems kernel arguments: rounds, K s_0, batch K V
+  float* b_tc_part = nullptr;      // split partial sums of all problems
+  int* b_tc_cnt = nullptr;         // split counters of all problems (zero between launches)
+  std::vector<int> b_tc_nsplit;
+  std::vector<size_t> b_tc_part_off, b_tc_cnt_off;
 
   // posterior predictive (ulisse_predict): the prescaled test inputs
   void* pred_xs = nullptr;
@@ -315,7 +324,7 @@ static ulisse_status prescale(ulisse_ctx* ctx) {
                           ctx->bneg, ctx->num_sms, ctx->stream));
     CK(launch_pack_x_tf32((const float*)ctx->xhat, ctx->bneg, ctx->params, ctx->DP, ctx->n,
                           ctx->ld128, ctx->Xt_hi, ctx->Xt_lo, ctx->ld128 * 24, ctx->num_sms,
-                          ctx->stream));
+                          ctx->stream, !ctx->tc_no_aug));
     if (!ctx->capturing) ctx->launches += 2;
   }
   return ULISSE_OK;
@@ -1991,8 +2000,8 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
   if (n_problems < 1 || n_problems > 4096 || !n || !d || !X || !y || !cfg)
     return fail(nullptr, ULISSE_ERR_ARG, "bad batch description");
   if (check_cfg(cfg) != ULISSE_OK) return fail(nullptr, ULISSE_ERR_ARG, "invalid config");
-  if (cfg->precision != ULISSE_PREC_FP32)
-    return fail(nullptr, ULISSE_ERR_ARG, "batched contexts run the FP32 path");
+  if (cfg->precision != ULISSE_PREC_FP32 && cfg->precision != ULISSE_PREC_MIXED)
+    return fail(nullptr, ULISSE_ERR_ARG, "batched contexts run the FP32 or the mixed path");
   if (cfg->n_probes > 16) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take n_probes <= 16");
   for (int b = 0; b < n_problems; ++b)
     if (d[b] < 1 || d[b] > kBatchMaxDP) return fail(nullptr, ULISSE_ERR_ARG, "batched contexts take d <= 8");
@@ -2022,6 +2031,7 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
       ctx->err = "problem " + std::to_string(b) + ": " + g_create_error;
       return bail(s);
     }
+    sub->tc_no_aug = true;   // the batched tensor-core K V adds b_j in its epilogue
     ctx->subs.push_back(sub);
     ctx->sub_p_off.push_back(poff);
     poff += d[b] + 2;
@@ -2050,6 +2060,49 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_g), sizeof(double) * kMaxP * n_problems)) ||
       (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->status_dev), sizeof(int))))
     return bail(s);
+  if (cfg->precision == ULISSE_PREC_MIXED) {
+    // tensor-core K V work list: per problem its 128-row blocks times a split of the j range
+    // into ranges of about kTcBatchTiles 32-point tiles; the longest ranges first
+    constexpr long long kTcBatchTiles = 256;
+    std::vector<int4> tci;
+    std::vector<std::pair<long long, int>> order;
+    size_t part = 0, cnt = 0;
+    for (int b = 0; b < n_problems; ++b) {
+      const long long nt = (n[b] + 31) / 32, nrb = (n[b] + 127) / 128;
+      int ns = (int)std::min<long long>(64, (nt + kTcBatchTiles - 1) / kTcBatchTiles);
+      const long long tps = (nt + ns - 1) / ns;
+      ns = (int)((nt + tps - 1) / tps);
+      ctx->b_tc_nsplit.push_back(ns);
+      ctx->b_tc_part_off.push_back(part);
+      ctx->b_tc_cnt_off.push_back(cnt);
+      if (ns > 1) part += (size_t)nrb * ns * 32 * 128;
+      cnt += (size_t)nrb;
+      order.push_back({tps, b});
+    }
+    std::stable_sort(order.begin(), order.end(),
+                     [](const std::pair<long long, int>& a, const std::pair<long long, int>& c) {
+                       return a.first > c.first;
+                     });
+    for (const auto& o : order) {
+      const int b = o.second;
+      const int nrb = (int)((n[b] + 127) / 128);
+      for (int rb = 0; rb < nrb; ++rb)
+        for (int sp = 0; sp < ctx->b_tc_nsplit[b]; ++sp) tci.push_back(make_int4(b, rb, sp, 0));
+    }
+    ctx->b_tc_n_items = (int)tci.size();
+    if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_items), sizeof(int4) * tci.size())) ||
+        (s = dev_alloc(ctx, &ctx->b_tc_args, 3 * tc2_batch_args_bytes(n_problems))) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_part), sizeof(float) * std::max<size_t>(part, 1))) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_cnt), sizeof(int) * cnt)))
+      return bail(s);
+    if (cudaMemsetAsync(ctx->b_tc_cnt, 0, sizeof(int) * cnt, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->b_tc_items, tci.data(), sizeof(int4) * tci.size(),
+                        cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+      ctx->err = "upload of the tensor-core work list failed";
+      return bail(ULISSE_ERR_CUDA);
+    }
+  }
   if (cudaMallocHost(&ctx->b_h_nlive, sizeof(int) * n_problems) != cudaSuccess ||
       cudaMallocHost(&ctx->b_h_status, sizeof(int) * (n_problems + 1)) != cudaSuccess ||
       cudaMallocHost(&ctx->h_status, sizeof(int)) != cudaSuccess) {
@@ -2123,6 +2176,56 @@ static ulisse_status batch_clear_status(ulisse_ctx* ctx) {
     }                                         \
   } while (0)
 
+extern "C++" {
+// Kernel arguments of the batched tensor-core K V into slot k of b_tc_args (0: the CG
+// rounds, 1: K s_0 of warm-started solves, 2: ulisse_batch_kmv): cols(b, sub, L) sets each
+// problem's V, vmap, R or R_dev, U and umap; the rest is the problem's own operand buffers.
+template <typename Fn>
+static ulisse_status batch_tc_upload(ulisse_ctx* ctx, int k, Fn cols) {
+  const int B = (int)ctx->subs.size();
+  std::vector<TcLaunch> L((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    ulisse_ctx* sub = ctx->subs[b];
+    TcLaunch l{};
+    cols(b, sub, l);
+    l.ldv = sub->ldn;
+    l.ldu = sub->ldn;
+    l.xhat = (const float*)sub->xhat;
+    l.bneg = sub->bneg;
+    l.V_hi = sub->Vt_hi;
+    l.V_lo = sub->Vt_lo;
+    l.n = sub->n;
+    l.DP = sub->DP;
+    l.params = sub->params;
+    l.nsplit = ctx->b_tc_nsplit[b];
+    l.partials = ctx->b_tc_part + ctx->b_tc_part_off[b];
+    l.counters = ctx->b_tc_cnt + ctx->b_tc_cnt_off[b];
+    l.status = ctx->status_dev;
+    l.X_hi = sub->Xt_hi;
+    l.X_lo = sub->Xt_lo;
+    l.X_off = sub->ld128 * 24;
+    L[b] = l;
+  }
+  CK(tc2_batch_upload_args(L.data(), B, (char*)ctx->b_tc_args + k * tc2_batch_args_bytes(B),
+                           ctx->stream));
+  return ULISSE_OK;
+}
+
+// One batched K V over all problems: the tensor-core launch (slot of its arguments) or the
+// persistent FP32 launch (its descriptor array), for at most r_max live columns.
+static cudaError_t batch_kv_launch(ulisse_ctx* ctx, int slot, BatchKmvDesc* desc, int r_max,
+                                   cudaStream_t st) {
+  const int B = (int)ctx->subs.size();
+  if (ctx->cfg.precision == ULISSE_PREC_MIXED)
+    return launch_kmv_tc2_batch((char*)ctx->b_tc_args + slot * tc2_batch_args_bytes(B), B,
+                                ctx->b_tc_items, ctx->b_tc_n_items, r_max, st);
+  return launch_kmv_batch(desc, ctx->b_items, ctx->b_n_items, ctx->b_queue,
+                          kBatchWidths[batch_width_bucket(r_max)], ctx->num_sms,
+                          ctx->status_dev, st);
+}
+
+}  // extern "C++"
+
 ulisse_status ulisse_batch_kmv(ulisse_ctx* ctx, const double* psi, const float* const* V, int R,
                                float* const* U) {
   BATCHED_ONLY(ctx);
@@ -2151,8 +2254,19 @@ ulisse_status ulisse_batch_kmv(ulisse_ctx* ctx, const double* psi, const float* 
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_rcount, rc.data(), sizeof(int) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
-  CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue, R, ctx->num_sms,
-                      ctx->status_dev, ctx->stream));
+  if (ctx->cfg.precision == ULISSE_PREC_MIXED) {
+    CKS(batch_tc_upload(ctx, 2, [R](int, ulisse_ctx* sub, TcLaunch& l) {
+      l.V = sub->D;
+      l.vmap = sub->iota;
+      l.R = R;
+      l.U = sub->KD;
+      l.umap = sub->iota;
+    }));
+    CK(batch_kv_launch(ctx, 2, nullptr, R, ctx->stream));
+  } else {
+    CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue, R,
+                        ctx->num_sms, ctx->status_dev, ctx->stream));
+  }
   ctx->launches++;
   ctx->mvp_rounds++;
   ctx->entry_rhs += entries;
@@ -2267,6 +2381,23 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
                      ctx->stream));
   CK(cudaMemcpyAsync(ctx->b_gdesc, gd.data(), sizeof(BatchGradDesc) * B, cudaMemcpyHostToDevice,
                      ctx->stream));
+  if (ctx->cfg.precision == ULISSE_PREC_MIXED) {
+    prime_kmv_tc2_batch();
+    CKS(batch_tc_upload(ctx, 0, [](int, ulisse_ctx* sub, TcLaunch& l) {
+      l.V = sub->D;
+      l.vmap = sub->live;
+      l.R_dev = sub->n_live_dev;
+      l.U = sub->KD;
+      l.umap = sub->live;
+    }));
+    CKS(batch_tc_upload(ctx, 1, [ctx](int b, ulisse_ctx* sub, TcLaunch& l) {
+      l.V = sub->S;
+      l.vmap = sub->warm_map;
+      l.R_dev = ctx->b_rcount + b;
+      l.U = sub->KD;
+      l.umap = sub->iota;
+    }));
+  }
   return ULISSE_OK;
 }
 
@@ -2297,10 +2428,7 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
   CK(cudaGetLastError());
   // warm-started solves: every problem's K s_0 in one persistent launch, then the starts
   const bool warm = ctx->cfg.warm_start_probes != 0;
-  if (warm)
-    CK(launch_kmv_batch(ctx->b_kdesc0, ctx->b_items, ctx->b_n_items, ctx->b_queue,
-                        kBatchWidths[batch_width_bucket(R)], ctx->num_sms, ctx->status_dev,
-                        ctx->stream));
+  if (warm) CK(batch_kv_launch(ctx, 1, ctx->b_kdesc0, R, ctx->stream));
   for (int b = 0; b < B; ++b) {
     ulisse_ctx* sub = ctx->subs[b];
     CgArgs<float> a = cg_args<float>(sub, 0, 0);
@@ -2329,9 +2457,7 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
       CK(cudaStreamSynchronize(ctx->stream));
       const int rmax = *ctx->b_h_rmax;
       if (rmax == 0) break;
-      CK(launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items, ctx->b_queue,
-                          kBatchWidths[batch_width_bucket(rmax)], ctx->num_sms, ctx->status_dev,
-                          ctx->stream));
+      CK(batch_kv_launch(ctx, 0, ctx->b_kdesc, rmax, ctx->stream));
       CK(cg_round(ctx->stream));
     }
   } else {
@@ -2382,9 +2508,7 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
     for (int k = 0; k < 5; ++k) {
       CK(cudaStreamBeginCaptureToGraph(s2, sp.conditional.phGraph_out[k], nullptr, nullptr, 0,
                                        cudaStreamCaptureModeThreadLocal));
-      const cudaError_t e3 = launch_kmv_batch(ctx->b_kdesc, ctx->b_items, ctx->b_n_items,
-                                              ctx->b_queue, kBatchWidths[k], ctx->num_sms,
-                                              ctx->status_dev, s2);
+      const cudaError_t e3 = batch_kv_launch(ctx, 0, ctx->b_kdesc, kBatchWidths[k], s2);
       const cudaError_t e4 = cudaStreamEndCapture(s2, &tmp);
       CK(e3);
       CK(e4);
@@ -2827,7 +2951,9 @@ void ulisse_destroy(ulisse_ctx* ctx) {
   for (void** p : {reinterpret_cast<void**>(&ctx->b_items), reinterpret_cast<void**>(&ctx->b_kdesc),
                    reinterpret_cast<void**>(&ctx->b_gdesc), reinterpret_cast<void**>(&ctx->b_queue),
                    reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),
-                   reinterpret_cast<void**>(&ctx->b_gpart), reinterpret_cast<void**>(&ctx->b_g)})
+                   reinterpret_cast<void**>(&ctx->b_gpart), reinterpret_cast<void**>(&ctx->b_g),
+                   reinterpret_cast<void**>(&ctx->b_tc_items), &ctx->b_tc_args,
+                   reinterpret_cast<void**>(&ctx->b_tc_part), reinterpret_cast<void**>(&ctx->b_tc_cnt)})
     dev_free(*p);
   if (ctx->b_h_nlive) cudaFreeHost(ctx->b_h_nlive);
   if (ctx->b_h_status) cudaFreeHost(ctx->b_h_status);

@@ -30,6 +30,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "kmv_kernel.cuh"
 #include "tc_common.cuh"
@@ -43,10 +44,11 @@ constexpr uint32_t kT2Cols = 128;  // tensor-memory columns per CTA
 
 // The rows A_j = [x^_j, 1, 0...] and B_j = [2 c1 x^_j, b_j, 0...] for j in [0, rows) as TF32
 // high part and remainder, K8 columns, in 32-row K-major canonical tiles; rows >= n are zero.
-// When K8 == DP there is no slot for the augmented column (A_j = x^_j, B_j = 2 c1 x^_j).
+// When K8 == DP there is no slot for the augmented column (A_j = x^_j, B_j = 2 c1 x^_j); the
+// batched launches leave it out for every d (aug = 0) and add b_j in the epilogue.
 // b_j = -c1 |x^_j|^2 is read from the row norms of launch_prescale_tc.
 __global__ void pack_x_tf32_kernel(const float* __restrict__ xhat, const float* __restrict__ bneg,
-                                   const DevParams* __restrict__ params, int DP, int K8,
+                                   const DevParams* __restrict__ params, int DP, int K8, int aug,
                                    long long n, long long rows, float* __restrict__ Ahi,
                                    float* __restrict__ Alo, float* __restrict__ Bhi,
                                    float* __restrict__ Blo) {
@@ -60,7 +62,7 @@ __global__ void pack_x_tf32_kernel(const float* __restrict__ xhat, const float* 
       if (k < DP) {
         va = xhat[j * DP + k];
         vb = two_c1 * va;
-      } else if (k == DP) {
+      } else if (k == DP && aug) {
         va = 1.f;
         vb = bneg[j];
       }
@@ -88,6 +90,7 @@ struct Tc2DevArgs {
   long long ldv;
   const int* vmap;
   int R;
+  const int* R_dev;      // batched launches: the live column count on the device (else null)
   float* U;
   long long ldu;
   const int* umap;
@@ -149,8 +152,11 @@ __device__ inline void t2_ld_cols(uint32_t taddr, float (&v)[NH]) {
   }
 }
 
+// One CTA's work: row block rb, j-range split sp, R live columns.  Shared by the
+// single-problem kernel (rb, sp from the block index) and the batched one (from its work list).
 template <int K8, int N, bool BJ>
-__global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs a) {
+__device__ __forceinline__ void tc2_body(const Tc2DevArgs& a, const int rb, const int sp,
+                                         const int R) {
   using S = Tc2Shape<K8, N, BJ>;
   constexpr int ST = S::ST;
   constexpr int NB = S::NB;
@@ -172,8 +178,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
   auto stage = [&](int s) -> unsigned char* { return smem + S::OFF_STAGES + s * S::STAGE_BYTES; };
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rb = blockIdx.x / a.nsplit;
-  const int sp = blockIdx.x - rb * a.nsplit;
+  const long long slot = (long long)rb * a.nsplit + sp;   // this CTA's partial-sum slot
   const long long row0 = (long long)rb * kT2BM;
   const int tile_begin = sp * a.tiles_per_split;
   const int nt = max(0, min(tile_begin + a.tiles_per_split, a.ntiles) - tile_begin);
@@ -353,18 +358,18 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
 #pragma unroll
           for (int q = 0; q < NH; ++q) {
             const int r = half * NH + q;
-            if (r < a.R)
+            if (r < R)
               a.U[(long long)a.umap[r] * a.ldu + i] =
                   fmaf(lam, a.V[(long long)a.vmap[r] * a.ldv + i], u[q]);
           }
         }
       } else {
-        float* part = a.partials + (long long)blockIdx.x * N * kT2BM;
+        float* part = a.partials + slot * N * kT2BM;
 #pragma unroll
         for (int q = 0; q < NH; ++q) part[(half * NH + q) * kT2BM + il] = u[q];
       }
     } else if (ok && a.nsplit > 1) {
-      float* part = a.partials + (long long)blockIdx.x * N * kT2BM;
+      float* part = a.partials + slot * N * kT2BM;
 #pragma unroll
       for (int q = 0; q < NH; ++q) part[(half * NH + q) * kT2BM + il] = 0.f;
     }
@@ -398,7 +403,7 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
   __threadfence();
   const float* base = a.partials + (long long)rb * a.nsplit * N * kT2BM;
   const float lam = (float)a.params->lambda;
-  for (int idx = tid; idx < a.R * kT2BM; idx += kT2Threads) {
+  for (int idx = tid; idx < R * kT2BM; idx += kT2Threads) {
     const int r = idx / kT2BM, il = idx - r * kT2BM;
     const long long i = row0 + il;
     if (i >= a.n) continue;
@@ -407,6 +412,51 @@ __global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs
     a.U[(long long)a.umap[r] * a.ldu + i] = fmaf(lam, a.V[(long long)a.vmap[r] * a.ldv + i], u);
   }
   if (tid == 0) a.counters[rb] = 0;
+}
+
+template <int K8, int N, bool BJ>
+__global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_kernel(const Tc2DevArgs a) {
+  const int rb = blockIdx.x / a.nsplit;
+  tc2_body<K8, N, BJ>(a, rb, blockIdx.x - rb * a.nsplit, a.R);
+}
+
+// Many problems in one launch: CTA b takes work item items[b] = (problem, row block, split)
+// with that problem's arguments; a problem with no live columns is skipped.
+template <int K8, int N, bool BJ>
+__global__ void __launch_bounds__(kT2Threads, 4) kmv_tc2_batch_kernel(
+    const Tc2DevArgs* __restrict__ args, const int4* __restrict__ items) {
+  __shared__ Tc2DevArgs s_a;
+  const int4 it = items[blockIdx.x];
+  if (threadIdx.x == 0) s_a = args[it.x];
+  __syncthreads();
+  const int R = s_a.R_dev ? *s_a.R_dev : s_a.R;
+  if (R <= 0) return;
+  tc2_body<K8, N, BJ>(s_a, it.y, it.z, R);
+}
+
+// The BF16 high and low parts of every problem's live V columns (as pack_v_kernel, one
+// problem per grid row): K-major canonical images of N rows (columns of V) x 32 points.
+__global__ void pack_v_batch_kernel(const Tc2DevArgs* __restrict__ args, int N) {
+  const Tc2DevArgs& a = args[blockIdx.y];
+  const int R = a.R_dev ? *a.R_dev : a.R;
+  if (R <= 0) return;
+  const long long ntiles = a.ntiles;
+  const long long per_tile = (long long)N * kT2BN;
+  __nv_bfloat16* Vhi = const_cast<__nv_bfloat16*>(a.V_hi);
+  __nv_bfloat16* Vlo = const_cast<__nv_bfloat16*>(a.V_lo);
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < ntiles * per_tile;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long t = idx / per_tile;
+    const int rem = (int)(idx - t * per_tile);
+    const int r = rem / kT2BN, jj = rem - r * kT2BN;
+    const long long j = t * kT2BN + jj;
+    const float v = (r < R && j < a.n) ? a.V[(long long)a.vmap[r] * a.ldv + j] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const __nv_bfloat16 l = __float2bfloat16_rn(v - __bfloat162float(h));
+    const long long off = t * per_tile + tc::canon_offset(r, jj, 2, kT2BN / 8) / 2;
+    Vhi[off] = h;
+    Vlo[off] = l;
+  }
 }
 
 template <int K8, int N, bool BJ>
@@ -460,6 +510,7 @@ struct Tc2Inst {
     a.ldv = L.ldv;
     a.vmap = L.vmap;
     a.R = L.R;
+    a.R_dev = nullptr;
     a.U = static_cast<float*>(L.U);
     a.ldu = L.ldu;
     a.umap = L.umap;
@@ -505,13 +556,90 @@ cudaError_t launch_kmv_tc2(TcLaunch& L, cudaStream_t s) {
 
 cudaError_t launch_pack_x_tf32(const float* xhat, const float* bneg, const DevParams* params,
                                int DP, long long n, long long ld128, float* X_hi, float* X_lo,
-                               long long X_off, int num_sms, cudaStream_t s) {
+                               long long X_off, int num_sms, cudaStream_t s, bool aug) {
   const int K8 = tc2_k8(DP);
   const long long total = ld128 * K8;
   const int blocks = (int)std::min<long long>((total + 255) / 256, 8LL * num_sms);
-  pack_x_tf32_kernel<<<blocks, 256, 0, s>>>(xhat, bneg, params, DP, K8, n, ld128, X_hi, X_lo,
-                                            X_hi + X_off, X_lo + X_off);
+  pack_x_tf32_kernel<<<blocks, 256, 0, s>>>(xhat, bneg, params, DP, K8, aug ? 1 : 0, n, ld128,
+                                            X_hi, X_lo, X_hi + X_off, X_lo + X_off);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched launches: many problems' K V in one launch (padded d <= 8, K8 = 8, b_j in the
+// epilogue, the rows packed without the augmented column).
+// ---------------------------------------------------------------------------------------
+size_t tc2_batch_args_bytes(int B) { return sizeof(Tc2DevArgs) * (size_t)B; }
+
+cudaError_t tc2_batch_upload_args(const TcLaunch* L, int B, void* args_dev, cudaStream_t s) {
+  std::vector<Tc2DevArgs> h((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    const TcLaunch& l = L[b];
+    if (l.DP > 8 || l.nsplit < 1) return cudaErrorInvalidValue;
+    Tc2DevArgs& a = h[b];
+    const long long ntiles = (l.n + kT2BN - 1) / kT2BN;
+    a.A_hi = l.X_hi;
+    a.A_lo = l.X_lo;
+    a.B_hi = l.X_hi + l.X_off;
+    a.B_lo = l.X_lo + l.X_off;
+    a.bneg = l.bneg;
+    a.V_hi = static_cast<const __nv_bfloat16*>(l.V_hi);
+    a.V_lo = static_cast<const __nv_bfloat16*>(l.V_lo);
+    a.V = static_cast<const float*>(l.V);
+    a.ldv = l.ldv;
+    a.vmap = l.vmap;
+    a.R = l.R;
+    a.R_dev = l.R_dev;
+    a.U = static_cast<float*>(l.U);
+    a.ldu = l.ldu;
+    a.umap = l.umap;
+    a.n = l.n;
+    a.params = l.params;
+    a.tiles_per_split = (int)((ntiles + l.nsplit - 1) / l.nsplit);
+    a.nsplit = (int)((ntiles + a.tiles_per_split - 1) / a.tiles_per_split);
+    if (a.nsplit != l.nsplit || a.tiles_per_split > kTcMaxSplitTiles) return cudaErrorInvalidValue;
+    a.ntiles = (int)ntiles;
+    a.partials = static_cast<float*>(l.partials);
+    a.counters = l.counters;
+    a.status = l.status;
+  }
+  return cudaMemcpyAsync(args_dev, h.data(), sizeof(Tc2DevArgs) * (size_t)B,
+                         cudaMemcpyHostToDevice, s);
+}
+
+template <int N>
+static void tc2_batch_prime() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto fn = kmv_tc2_batch_kernel<8, N, true>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)Tc2Shape<8, N, true>::SMEM);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+}
+
+void prime_kmv_tc2_batch() {
+  tc2_batch_prime<16>();
+  tc2_batch_prime<32>();
+}
+
+template <int N>
+static cudaError_t tc2_batch_launch(const Tc2DevArgs* args, int B, const int4* items,
+                                    int n_items, cudaStream_t s) {
+  tc2_batch_prime<N>();
+  pack_v_batch_kernel<<<dim3(64, (unsigned)B), 256, 0, s>>>(args, N);
+  if (n_items > 0)
+    kmv_tc2_batch_kernel<8, N, true><<<n_items, kT2Threads, Tc2Shape<8, N, true>::SMEM, s>>>(
+        args, items);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kmv_tc2_batch(const void* args_dev, int B, const int4* items, int n_items,
+                                 int R_max, cudaStream_t s) {
+  const Tc2DevArgs* args = static_cast<const Tc2DevArgs*>(args_dev);
+  if (B < 1 || R_max < 1 || R_max > 32) return cudaErrorInvalidValue;
+  return R_max <= 16 ? tc2_batch_launch<16>(args, B, items, n_items, s)
+                     : tc2_batch_launch<32>(args, B, items, n_items, s);
 }
 
 }  // namespace ulisse

@@ -277,6 +277,7 @@ struct TcLaunch {
   long long ldv;
   const int* vmap;
   int R;                 // right-hand sides (<= 64)
+  const int* R_dev;      // batched launches: the live column count on the device (or null)
   void* U;
   long long ldu;
   const int* umap;
@@ -315,9 +316,19 @@ cudaError_t launch_kmv_tc(TcLaunch& L, cudaStream_t s);
 cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s);
 cudaError_t launch_kmv_tc2(TcLaunch& L, cudaStream_t s);
 void launch_pack_v(const TcLaunch& L, int N, long long ntiles, cudaStream_t s);
+// aug: rows carry the column term b_j (padded d 2 and 4 of the single-problem launches);
+// false for the batched launches, whose epilogue adds it for every d.
 cudaError_t launch_pack_x_tf32(const float* xhat, const float* bneg, const DevParams* params,
                                int DP, long long n, long long ld128, float* X_hi, float* X_lo,
-                               long long X_off, int num_sms, cudaStream_t s);
+                               long long X_off, int num_sms, cudaStream_t s, bool aug);
+// Batched tensor-core K V (padded d <= 8): per problem a TcLaunch with the operand pointers,
+// R or R_dev, and the forced split nsplit >= 1 (tiles per split <= kTcMaxSplitTiles);
+// items: (problem, 128-row block, split) per CTA; R_max: the largest live column count.
+size_t tc2_batch_args_bytes(int B);
+cudaError_t tc2_batch_upload_args(const TcLaunch* L, int B, void* args_dev, cudaStream_t s);
+cudaError_t launch_kmv_tc2_batch(const void* args_dev, int B, const int4* items, int n_items,
+                                 int R_max, cudaStream_t s);
+void prime_kmv_tc2_batch();
 cudaError_t launch_prescale_tc(const float* xhat, int DP, int d, long long n, long long ld,
                                float* bneg, int num_sms, cudaStream_t s);
 

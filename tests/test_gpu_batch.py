@@ -168,8 +168,8 @@ def test_batch_argument_errors():
     probs = _short_problems()[:2]
     Xs = [torch.from_numpy(p.X).cuda() for p in probs]
     ys = [torch.from_numpy(p.y).cuda() for p in probs]
-    with pytest.raises(u.UlisseError):
-        u.BatchContext(Xs, ys, u.ulisse_config_default(precision=u.PREC_MIXED))
+    with pytest.raises(u.UlisseError):     # FP64 batches are not offered
+        u.BatchContext(Xs, ys, u.ulisse_config_default(precision=u.PREC_FP64))
     big = w.random_problem(100, 12, seed=1)
     with pytest.raises(u.UlisseError):
         _batch([probs[0], big])
