@@ -146,6 +146,15 @@ struct ulisse_ctx {
   int* b_tc_cnt = nullptr;         // split counters of all problems (zero between launches)
   std::vector<int> b_tc_nsplit;
   std::vector<size_t> b_tc_part_off, b_tc_cnt_off;
+  // ... and the tensor-core gradient pass, one launch per padded input width (group)
+  std::vector<std::vector<int>> b_gt_groups;   // problem indices of each width
+  std::vector<int> b_gt_dp, b_gt_item_off, b_gt_item_n;
+  std::vector<int> b_gt_nsplit;                // per problem
+  std::vector<size_t> b_gt_part_off;           // per problem, doubles
+  int4* b_gt_items = nullptr;
+  void* b_gt_args = nullptr;                   // problems in group order
+  double* b_gt_part = nullptr;
+  int* b_gt_cnt = nullptr;                     // one counter per problem
 
   // posterior predictive (ulisse_predict): the prescaled test inputs
   void* pred_xs = nullptr;
@@ -2090,12 +2099,56 @@ ulisse_status ulisse_create_batched(ulisse_ctx** out, int n_problems, const long
         for (int sp = 0; sp < ctx->b_tc_nsplit[b]; ++sp) tci.push_back(make_int4(b, rb, sp, 0));
     }
     ctx->b_tc_n_items = (int)tci.size();
+    // gradient pass: per width group the (problem, row block, split) items, most tiles first
+    // (row block rb visits the tiles [4 rb, ntiles): the symmetric pass)
+    std::vector<int4> gti;
+    size_t gpart = 0;
+    ctx->b_gt_nsplit.assign(n_problems, 1);
+    ctx->b_gt_part_off.assign(n_problems, 0);
+    for (int dp : {2, 4, 8}) {
+      std::vector<int> grp;
+      for (int b = 0; b < n_problems; ++b)
+        if ((d[b] <= 2 ? 2 : d[b] <= 4 ? 4 : 8) == dp) grp.push_back(b);
+      if (grp.empty()) continue;
+      std::vector<std::pair<long long, int4>> its;
+      for (int li = 0; li < (int)grp.size(); ++li) {
+        const int b = grp[li];
+        const long long nt = (n[b] + 31) / 32, nrb = (n[b] + 127) / 128;
+        const int ns = (int)std::min<long long>(64, (nt + 255) / 256);
+        ctx->b_gt_nsplit[b] = ns;
+        ctx->b_gt_part_off[b] = gpart;
+        gpart += (size_t)nrb * ns * kMaxP;
+        for (int rb = 0; rb < nrb; ++rb) {
+          const long long span = nt - 4LL * rb, per = (span + ns - 1) / ns;
+          for (int sp = 0; sp < ns; ++sp) {
+            const long long tiles = std::max<long long>(0, std::min(per, span - sp * per));
+            its.push_back({tiles, make_int4(li, rb, sp, 0)});
+          }
+        }
+      }
+      std::stable_sort(its.begin(), its.end(),
+                       [](const std::pair<long long, int4>& a, const std::pair<long long, int4>& c) {
+                         return a.first > c.first;
+                       });
+      ctx->b_gt_groups.push_back(grp);
+      ctx->b_gt_dp.push_back(dp);
+      ctx->b_gt_item_off.push_back((int)gti.size());
+      ctx->b_gt_item_n.push_back((int)its.size());
+      for (const auto& e : its) gti.push_back(e.second);
+    }
     if ((s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_items), sizeof(int4) * tci.size())) ||
         (s = dev_alloc(ctx, &ctx->b_tc_args, 3 * tc2_batch_args_bytes(n_problems))) ||
         (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_part), sizeof(float) * std::max<size_t>(part, 1))) ||
-        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_cnt), sizeof(int) * cnt)))
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_tc_cnt), sizeof(int) * cnt)) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_gt_items), sizeof(int4) * gti.size())) ||
+        (s = dev_alloc(ctx, &ctx->b_gt_args, gt_batch_args_bytes(n_problems))) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_gt_part), sizeof(double) * gpart)) ||
+        (s = dev_alloc(ctx, reinterpret_cast<void**>(&ctx->b_gt_cnt), sizeof(int) * n_problems)))
       return bail(s);
     if (cudaMemsetAsync(ctx->b_tc_cnt, 0, sizeof(int) * cnt, ctx->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->b_gt_cnt, 0, sizeof(int) * n_problems, ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(ctx->b_gt_items, gti.data(), sizeof(int4) * gti.size(),
+                        cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaMemcpyAsync(ctx->b_tc_items, tci.data(), sizeof(int4) * tci.size(),
                         cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
         cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
@@ -2397,6 +2450,45 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
       l.U = sub->KD;
       l.umap = sub->iota;
     }));
+    // the tensor-core gradient pass: per width group the problems' operands, in group order
+    int off = 0;
+    for (size_t g = 0; g < ctx->b_gt_groups.size(); ++g) {
+      const std::vector<int>& grp = ctx->b_gt_groups[g];
+      std::vector<GradLaunch> gl(grp.size());
+      std::vector<int> ns(grp.size());
+      for (size_t li = 0; li < grp.size(); ++li) {
+        const int b = grp[li];
+        ulisse_ctx* sub = ctx->subs[b];
+        GradLaunch L{};
+        L.xhat = sub->xhat;
+        L.n = sub->n;
+        L.ldn = sub->ldn;
+        L.d = sub->d;
+        L.DP = sub->DP;
+        L.A = sub->SE;
+        L.amap = sub->amap;
+        L.sa = sub->sa_dev;
+        L.B = sub->B;
+        L.bmap = sub->bmap;
+        L.ld = sub->ldn;
+        L.M = R;
+        L.params = sub->params;
+        L.partials = ctx->b_gt_part + ctx->b_gt_part_off[b];
+        L.counter = ctx->b_gt_cnt + b;
+        L.g_out = ctx->b_g + (long long)b * kMaxP;
+        L.status = ctx->status_dev;
+        L.bneg = sub->bneg;
+        L.tc_hi = sub->Gt_hi;
+        L.tc_lo = sub->Gt_lo;
+        L.tc_ld = sub->ld128;
+        gl[li] = L;
+        ns[li] = ctx->b_gt_nsplit[b];
+      }
+      CK(gt_batch_upload_args(gl.data(), ns.data(), (int)grp.size(),
+                              (char*)ctx->b_gt_args + off * gt_batch_args_bytes(1), ctx->stream));
+      CK(launch_grad_tc_batch(nullptr, 0, nullptr, 0, ctx->b_gt_dp[g], R, ctx->stream, true));
+      off += (int)grp.size();
+    }
   }
   return ULISSE_OK;
 }
@@ -2520,8 +2612,19 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
     CK(cudaMemcpyAsync(sub->B, (char*)sub->SE + sub->ldn * 4, sub->ldn * 4,
                        cudaMemcpyDeviceToDevice, ctx->stream));
   }
-  CK(launch_grad_batch(ctx->b_gdesc, B, ctx->b_items, ctx->b_n_items, ctx->b_queue, ctx->b_gpart,
-                       R, ctx->num_sms, ctx->status_dev, ctx->stream));
+  if (ctx->cfg.precision == ULISSE_PREC_MIXED) {
+    int off = 0;
+    for (size_t g = 0; g < ctx->b_gt_groups.size(); ++g) {
+      const int nb = (int)ctx->b_gt_groups[g].size();
+      CK(launch_grad_tc_batch((char*)ctx->b_gt_args + off * gt_batch_args_bytes(1), nb,
+                              ctx->b_gt_items + ctx->b_gt_item_off[g], ctx->b_gt_item_n[g],
+                              ctx->b_gt_dp[g], R, ctx->stream));
+      off += nb;
+    }
+  } else {
+    CK(launch_grad_batch(ctx->b_gdesc, B, ctx->b_items, ctx->b_n_items, ctx->b_queue,
+                         ctx->b_gpart, R, ctx->num_sms, ctx->status_dev, ctx->stream));
+  }
   if (sgld) {
     off = 0;
     for (int b = 0; b < B; ++b) {
@@ -2553,7 +2656,12 @@ static void batch_count_fixed(ulisse_ctx* ctx, int steps, bool sgld) {
   const bool warm = ctx->cfg.warm_start_probes != 0;
   double ent = 0.0;
   for (ulisse_ctx* sub : ctx->subs) ent += (double)sub->n * (double)sub->n * R;
-  ctx->launches += (long long)steps * (3LL * B + 2 + (sgld ? B + 1 : 0) + (warm ? 1 : 0));
+  // per problem prescale (+ the tensor-core row images), probes, CG start; the gradient
+  // sweep; the updates; the warm starts' product (mixed: every K V launch packs V first)
+  const bool mixed = ctx->cfg.precision == ULISSE_PREC_MIXED;
+  const long long grad_launches = mixed ? 2LL * (long long)ctx->b_gt_groups.size() : 2LL;
+  ctx->launches += (long long)steps * ((mixed ? 5LL : 3LL) * B + grad_launches +
+                                       (sgld ? B + 1 : 0) + (warm ? (mixed ? 2 : 1) : 0));
   ctx->entry_rhs += steps * ent * (warm ? 2.0 : 1.0);
   if (warm) ctx->mvp_rounds += steps;
 }
@@ -2565,6 +2673,8 @@ static ulisse_status batch_fold_gstat(ulisse_ctx* ctx) {
   ctx->mvp_rounds += ctx->h_gstat[0];
   ctx->entry_rhs += (double)ctx->h_gstat[1];
   ctx->launches += ctx->h_gstat[2];
+  // the device counts one K V launch per round; the mixed path also packs V each round
+  if (ctx->cfg.precision == ULISSE_PREC_MIXED) ctx->launches += ctx->h_gstat[0];
   CK(cudaMemsetAsync(ctx->gstat, 0, sizeof(long long) * 3, ctx->stream));
   return ULISSE_OK;
 }
@@ -2953,7 +3063,9 @@ void ulisse_destroy(ulisse_ctx* ctx) {
                    reinterpret_cast<void**>(&ctx->b_nlive), reinterpret_cast<void**>(&ctx->b_rcount),
                    reinterpret_cast<void**>(&ctx->b_gpart), reinterpret_cast<void**>(&ctx->b_g),
                    reinterpret_cast<void**>(&ctx->b_tc_items), &ctx->b_tc_args,
-                   reinterpret_cast<void**>(&ctx->b_tc_part), reinterpret_cast<void**>(&ctx->b_tc_cnt)})
+                   reinterpret_cast<void**>(&ctx->b_tc_part), reinterpret_cast<void**>(&ctx->b_tc_cnt),
+                   reinterpret_cast<void**>(&ctx->b_gt_items), &ctx->b_gt_args,
+                   reinterpret_cast<void**>(&ctx->b_gt_part), reinterpret_cast<void**>(&ctx->b_gt_cnt)})
     dev_free(*p);
   if (ctx->b_h_nlive) cudaFreeHost(ctx->b_h_nlive);
   if (ctx->b_h_status) cudaFreeHost(ctx->b_h_status);

@@ -35,6 +35,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "kmv_kernel.cuh"
 #include "tc_common.cuh"
@@ -131,6 +132,7 @@ struct GtDevArgs {
   int d;
   const DevParams* params;
   int nsplit, ntiles;
+  int n_cta;           // CTAs of this problem (row blocks x nsplit): the last one reduces
   double* partials;
   int* counter;
   double* g_out;
@@ -164,8 +166,10 @@ __device__ inline bool gt_warp_wait(uint64_t* bar, uint32_t parity) {
   return __all_sync(0xffffffffu, ok);
 }
 
+// One CTA's work: row block rb, split sp of its tile range.  Shared by the single-problem
+// kernel and the batched one.
 template <int DP, int KS>
-__global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(const GtDevArgs a) {
+__device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const int sp) {
   using S = GtShape<DP, KS>;
   constexpr int ST = S::ST, K1 = S::K1, N2 = S::N2;
   constexpr int NACC = DP + 2;
@@ -189,8 +193,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   // Row block rb visits the tiles [4 rb, ntiles) (its own four tiles, then every later
   // one), cut into nsplit equal ranges; CTAs start in row-block order, longest ranges first.
   constexpr int kTilesPerBlock = kGtBM / kGtBN;
-  const int rb = blockIdx.x / a.nsplit;
-  const int sp = blockIdx.x - rb * a.nsplit;
+  const long long slot = (long long)rb * a.nsplit + sp;   // this CTA's partial-sum slot
   const long long row0 = (long long)rb * kGtBM;
   const int diag_end = min(kTilesPerBlock * (rb + 1), a.ntiles);   // tiles of I itself
   const int span = a.ntiles - kTilesPerBlock * rb;
@@ -448,7 +451,7 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
     }
   }
   __syncthreads();
-  double* part = a.partials + (long long)blockIdx.x * kMaxP;
+  double* part = a.partials + slot * kMaxP;
   if (tid < NACC) {
     double v = 0.0;
     for (int ww = 0; ww < 8; ++ww) v += s_red[ww][tid];
@@ -459,17 +462,90 @@ __global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(c
   }
   __threadfence();
   __syncthreads();
-  if (tid == 0) *s_last = (atomicAdd(a.counter, 1) == (int)gridDim.x - 1);
+  if (tid == 0) *s_last = (atomicAdd(a.counter, 1) == a.n_cta - 1);
   __syncthreads();
   if (!*s_last) return;
   __threadfence();
   if (tid < a.d + 2) {
     double v = 0.0;
-    for (unsigned b = 0; b < gridDim.x; ++b) v += __ldcg(a.partials + (long long)b * kMaxP + tid);
+    for (int b = 0; b < a.n_cta; ++b) v += __ldcg(a.partials + (long long)b * kMaxP + tid);
     if (tid == a.d + 1) v *= a.params->lambda;
     a.g_out[tid] = v;
   }
   if (tid == 0) *a.counter = 0;
+}
+
+template <int DP, int KS>
+__global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_kernel(const GtDevArgs a) {
+  const int rb = blockIdx.x / a.nsplit;
+  gt_body<DP, KS>(a, rb, blockIdx.x - rb * a.nsplit);
+}
+
+// Many problems of one input width in one launch: CTA b takes work item items[b] =
+// (problem, row block, split) with that problem's arguments.
+template <int DP, int KS>
+__global__ void __launch_bounds__(kGtThreads, DP >= 16 ? 2 : 3) grad_tc_batch_kernel(
+    const GtDevArgs* __restrict__ args, const int4* __restrict__ items) {
+  __shared__ GtDevArgs s_a;
+  const int4 it = items[blockIdx.x];
+  if (threadIdx.x == 0) s_a = args[it.x];
+  __syncthreads();
+  gt_body<DP, KS>(s_a, it.y, it.z);
+}
+
+// The operand images of every problem of a batched launch (one problem per grid row), as
+// pack_bt_kernel and pack_z_kernel.
+template <int DP, int KS>
+__global__ void pack_gt_batch_kernel(const GtDevArgs* __restrict__ args) {
+  using S = GtShape<DP, KS>;
+  constexpr int K1 = S::K1, N2 = S::N2;
+  const GtDevArgs& a = args[blockIdx.y];
+  const long long ntiles = a.ntiles;
+  __nv_bfloat16* Bhi = const_cast<__nv_bfloat16*>(a.Bt_hi);
+  __nv_bfloat16* Blo = const_cast<__nv_bfloat16*>(a.Bt_lo);
+  __nv_bfloat16* Zhi = const_cast<__nv_bfloat16*>(a.Zt_hi);
+  __nv_bfloat16* Zlo = const_cast<__nv_bfloat16*>(a.Zt_lo);
+  const long long per_b = (long long)kGtBN * K1, per_z = (long long)N2 * kGtBN;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       idx < ntiles * (per_b + per_z); idx += (long long)gridDim.x * blockDim.x) {
+    __nv_bfloat16 h, l;
+    if (idx < ntiles * per_b) {
+      const long long t = idx / per_b;
+      const int rem = (int)(idx - t * per_b);
+      const int m = rem / kGtBN, j = rem - m * kGtBN;
+      const long long jj = t * kGtBN + j;
+      float v = 0.f;
+      if (jj < a.n) {
+        if (m < a.M) v = a.B[(long long)a.bmap[m] * a.ld + jj];
+        else if (m < 2 * a.M) v = a.sa[m - a.M] * a.A[(long long)a.amap[m - a.M] * a.ld + jj];
+      }
+      split_bf16(v, h, l);
+      const long long off = t * per_b + tc::canon_offset(j, m, 2, K1 / 8) / 2;
+      Bhi[off] = h;
+      Blo[off] = l;
+    } else {
+      const long long z = idx - ntiles * per_b;
+      const long long t = z / per_z;
+      const int rem = (int)(z - t * per_z);
+      const int c = rem / kGtBN, j = rem - c * kGtBN;
+      const long long jj = t * kGtBN + j;
+      float v = 0.f;
+      if (jj < a.n) {
+        if (c < DP) {
+          v = a.xhat[jj * DP + c];
+        } else if (c < 2 * DP) {
+          const float x = a.xhat[jj * DP + (c - DP)];
+          v = x * x;
+        } else if (c == 2 * DP) {
+          v = 1.f;
+        }
+      }
+      split_bf16(v, h, l);
+      const long long off = t * per_z + tc::canon_offset(c, j, 2, kGtBN / 8) / 2;
+      Zhi[off] = h;
+      Zlo[off] = l;
+    }
+  }
 }
 
 // Split of each row block's tile range into s CTAs.  The SMs share the visited tiles plus a
@@ -564,6 +640,7 @@ struct GtInst {
     a.d = L.d;
     a.params = L.params;
     a.nsplit = nsplit;
+    a.n_cta = n_rb * nsplit;
     a.ntiles = (int)ntiles;
     a.partials = L.partials;
     a.counter = L.counter;
@@ -583,6 +660,98 @@ static cudaError_t grad_tc_dispatch_m(GradLaunch& L, cudaStream_t s) {
   if (L.M <= 32) return GtInst<DP, 4>::launch(L, s);
   if (L.M <= 64) return GtInst<DP, 8>::launch(L, s);
   return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------------------
+// Batched launches: many problems of one padded width in one launch.
+// ---------------------------------------------------------------------------------------
+size_t gt_batch_args_bytes(int B) { return sizeof(GtDevArgs) * (size_t)B; }
+
+cudaError_t gt_batch_upload_args(const GradLaunch* L, const int* nsplit, int B, void* args_dev,
+                                 cudaStream_t s) {
+  std::vector<GtDevArgs> h((size_t)B);
+  for (int b = 0; b < B; ++b) {
+    const GradLaunch& l = L[b];
+    const long long ntiles = (l.n + kGtBN - 1) / kGtBN;
+    const long long n_rb = (l.n + kGtBM - 1) / kGtBM;
+    if (l.M < 1 || l.M > kMaxM || nsplit[b] < 1 || l.DP != L[0].DP || !l.tc_hi || !l.tc_lo ||
+        (ntiles + nsplit[b] - 1) / nsplit[b] > kTcMaxSplitTiles)
+      return cudaErrorInvalidValue;
+    GtDevArgs& a = h[b];
+    __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(l.tc_hi);
+    __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(l.tc_lo);
+    const long long zoff = (long long)kGtZOff * l.tc_ld;
+    a.xhat = static_cast<const float*>(l.xhat);
+    a.bneg = l.bneg;
+    a.Bt_hi = hi;
+    a.Bt_lo = lo;
+    a.Zt_hi = hi + zoff;
+    a.Zt_lo = lo + zoff;
+    a.A = static_cast<const float*>(l.A);
+    a.amap = l.amap;
+    a.sa = static_cast<const float*>(l.sa);
+    a.B = static_cast<const float*>(l.B);
+    a.bmap = l.bmap;
+    a.ld = l.ld;
+    a.M = l.M;
+    a.n = l.n;
+    a.d = l.d;
+    a.params = l.params;
+    a.nsplit = nsplit[b];
+    a.ntiles = (int)ntiles;
+    a.n_cta = (int)(n_rb * nsplit[b]);
+    a.partials = l.partials;
+    a.counter = l.counter;
+    a.g_out = l.g_out;
+    a.status = l.status;
+  }
+  return cudaMemcpyAsync(args_dev, h.data(), sizeof(GtDevArgs) * (size_t)B,
+                         cudaMemcpyHostToDevice, s);
+}
+
+template <int DP, int KS>
+static void gt_batch_prime() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto fn = grad_tc_batch_kernel<DP, KS>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)GtShape<DP, KS>::SMEM);
+    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  });
+}
+
+template <int DP, int KS>
+static cudaError_t gt_batch_launch(const GtDevArgs* args, int B, const int4* items, int n_items,
+                                   bool prime_only, cudaStream_t s) {
+  gt_batch_prime<DP, KS>();
+  if (prime_only) return cudaSuccess;
+  pack_gt_batch_kernel<DP, KS><<<dim3(64, (unsigned)B), 256, 0, s>>>(args);
+  if (n_items > 0)
+    grad_tc_batch_kernel<DP, KS><<<n_items, kGtThreads, GtShape<DP, KS>::SMEM, s>>>(args, items);
+  return cudaGetLastError();
+}
+
+template <int DP>
+static cudaError_t gt_batch_dispatch_m(const GtDevArgs* args, int B, const int4* items,
+                                       int n_items, int M, bool prime_only, cudaStream_t s) {
+  if (M <= 8) return gt_batch_launch<DP, 1>(args, B, items, n_items, prime_only, s);
+  if (M <= 16) return gt_batch_launch<DP, 2>(args, B, items, n_items, prime_only, s);
+  if (M <= 24) return gt_batch_launch<DP, 3>(args, B, items, n_items, prime_only, s);
+  if (M <= 32) return gt_batch_launch<DP, 4>(args, B, items, n_items, prime_only, s);
+  if (M <= 64) return gt_batch_launch<DP, 8>(args, B, items, n_items, prime_only, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_grad_tc_batch(const void* args_dev, int B, const int4* items, int n_items,
+                                 int DP, int M, cudaStream_t s, bool prime_only) {
+  const GtDevArgs* args = static_cast<const GtDevArgs*>(args_dev);
+  if (B < 1 && !prime_only) return cudaErrorInvalidValue;
+  switch (DP) {
+    case 2: return gt_batch_dispatch_m<2>(args, B, items, n_items, M, prime_only, s);
+    case 4: return gt_batch_dispatch_m<4>(args, B, items, n_items, M, prime_only, s);
+    case 8: return gt_batch_dispatch_m<8>(args, B, items, n_items, M, prime_only, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s) {

@@ -329,6 +329,15 @@ cudaError_t tc2_batch_upload_args(const TcLaunch* L, int B, void* args_dev, cuda
 cudaError_t launch_kmv_tc2_batch(const void* args_dev, int B, const int4* items, int n_items,
                                  int R_max, cudaStream_t s);
 void prime_kmv_tc2_batch();
+// Batched tensor-core gradient pass (problems of one padded width DP <= 8, M factor pairs):
+// per problem a GradLaunch with the operands (as launch_grad_tc) and its split nsplit[b];
+// items: (problem, 128-row block, split) per CTA.  prime_only: set the kernel attributes
+// (ahead of a capture) and launch nothing.
+size_t gt_batch_args_bytes(int B);
+cudaError_t gt_batch_upload_args(const GradLaunch* L, const int* nsplit, int B, void* args_dev,
+                                 cudaStream_t s);
+cudaError_t launch_grad_tc_batch(const void* args_dev, int B, const int4* items, int n_items,
+                                 int DP, int M, cudaStream_t s, bool prime_only = false);
 cudaError_t launch_prescale_tc(const float* xhat, int DP, int d, long long n, long long ld,
                                float* bneg, int num_sms, cudaStream_t s);
 

@@ -4,7 +4,8 @@ block, j-range split)), warm-started solves and one graph launch per batched ste
 problem is checked against the FP64 oracle with the generator seed the batch gives it
 (cfg.seed + b), at the mixed path's tolerances: every K V entry within 1e-4 of its
 dot-product scale sum_j |K_ij| |V_jr|, seeded gradients within 1e-4 (as the single-context
-mixed parity tests).  The batched gradient sweep is the FP32 one."""
+mixed parity tests).  The gradient sweep runs on the tensor cores too, one launch per padded
+input width (2, 4, 8) over (problem, row block, split) items."""
 import math
 
 import numpy as np
