@@ -98,3 +98,47 @@ def test_noalloc_rejects_oversized_requests():
                                      ctypes.c_void_p(V.data_ptr()), 1,
                                      ctypes.c_void_p(V.data_ptr()), None)
     assert too_big == u.ULISSE_ERR_ARG
+
+
+def test_noalloc_timing_against_context_entry_point():
+    """Times the two entry points with CUDA events at the test sizes (FP32 context path).
+    The allocation-free call plans its j-range split for the SMs whose partial sums fit
+    the static array, so it can be slower than the context path; this test prints both
+    times and only checks that the call completes."""
+    lib = u.load()
+    for n, R in ((9_937, 17), (50_000, 17)):
+        prob = w.census_like(n=n, d=8, seed=5)
+        X = torch.from_numpy(prob.X).cuda()
+        y = torch.from_numpy(prob.y).cuda()
+        V = torch.randn((n, R), device="cuda")
+        Vc = V.t().contiguous()
+        U = torch.empty((R, n), device="cuda")
+        psi = np.ascontiguousarray(prob.psi_true, dtype=np.float64)
+        stream = torch.cuda.current_stream()
+
+        def na():
+            st = lib.ulisse_kmv_noalloc(ctypes.c_void_p(X.data_ptr()), n, 8,
+                                        psi.ctypes.data_as(ctypes.c_void_p), -1,
+                                        ctypes.c_void_p(Vc.data_ptr()), R,
+                                        ctypes.c_void_p(U.data_ptr()),
+                                        ctypes.c_void_p(stream.cuda_stream))
+            assert st == u.ULISSE_OK
+
+        def timed(fn, reps=5):
+            fn()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            return sorted(ts)[len(ts) // 2]
+
+        t_na = timed(na)
+        assert u.ulisse_kmv_noalloc_status() == 0
+        with u.Context(X, y, u.ulisse_config_default()) as ctx:
+            Ucx = torch.empty((R, n), device="cuda").t()
+            t_cx = timed(lambda: ctx.kmv(prob.psi_true, V, out=Ucx))
+        print("K V n=%d R=%d: allocation-free %.3f ms, context %.3f ms" % (n, R, t_na, t_cx))
