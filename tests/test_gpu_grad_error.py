@@ -5,8 +5,8 @@ The parameters are the generating ones shifted by +0.3 in every log coordinate (
 generating parameters the exact gradient is close to zero and the ratio is meaningless).
 Both paths run the same seeds -- the same probes and the same truncation draws -- so they
 differ only by their arithmetic; the learned warm start is measured on the mixed path too
-(reported, not bounded: its unbiasedness is tested in test_gpu_warm_start.py).  The printed
-table is what profiles/grad_error_census_like.txt records."""
+(reported, not bounded: its unbiasedness is tested in test_gpu_warm_start.py).  bench.py
+measures the same statistic in its run (key gradient_error)."""
 import numpy as np
 import pytest
 
