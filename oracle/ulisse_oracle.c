@@ -150,14 +150,17 @@ void orc_kmv(const double *X, long n, int d, const double *psi, int which,
     orc_theta t = unpack(psi, d);
 #pragma omp parallel for schedule(static)
     for (long i = 0; i < n; ++i) {
+        /* every column, in blocks of 512 accumulators */
         double acc[512];
-        int Rc = R < 512 ? R : 512;
-        for (int r = 0; r < Rc; ++r) acc[r] = 0.0;
-        for (long j = 0; j < n; ++j) {
-            double a = entry(X, i, j, &t, which);
-            for (int r = 0; r < Rc; ++r) acc[r] += a * V[(long)r * n + j];
+        for (int r0 = 0; r0 < R; r0 += 512) {
+            const int Rc = R - r0 < 512 ? R - r0 : 512;
+            for (int r = 0; r < Rc; ++r) acc[r] = 0.0;
+            for (long j = 0; j < n; ++j) {
+                double a = entry(X, i, j, &t, which);
+                for (int r = 0; r < Rc; ++r) acc[r] += a * V[(long)(r0 + r) * n + j];
+            }
+            for (int r = 0; r < Rc; ++r) U[(long)(r0 + r) * n + i] = acc[r];
         }
-        for (int r = 0; r < Rc; ++r) U[(long)r * n + i] = acc[r];
     }
 }
 

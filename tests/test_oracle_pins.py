@@ -174,7 +174,7 @@ def test_dK_closed_forms(orc):
         assert np.all(np.diag(orc.cov_matrix(X, psi, which=q)) == 0.0)
 
 
-@pytest.mark.parametrize("n,d,R", [(1, 1, 1), (5, 2, 3), (67, 3, 4), (130, 8, 2)])
+@pytest.mark.parametrize("n,d,R", [(1, 1, 1), (5, 2, 3), (67, 3, 4), (130, 8, 2), (40, 2, 1100)])
 def test_kmv_vs_dense(orc, n, d, R):
     X = _rand_X(n, d, 4 + n)
     psi = np.concatenate([np.log(np.full(d, 0.5)), [np.log(1.2), np.log(0.1)]])
