@@ -28,6 +28,7 @@
  */
 #include <math.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -98,6 +99,10 @@ typedef struct {
 static orc_theta unpack(const double *psi, int d)
 {
     orc_theta t;
+    if (d < 1 || d > ORC_MAX_D) {
+        fprintf(stderr, "oracle: input width %d outside 1..%d\n", d, ORC_MAX_D);
+        abort();
+    }
     t.d = d;
     for (int k = 0; k < d; ++k) {
         double l = exp(psi[k]);
