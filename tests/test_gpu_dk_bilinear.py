@@ -78,8 +78,9 @@ def _check(orc, prob, M, precision, seed):
     assert rel.max() <= TOL[precision]
 
 
+# M covers every slot count of the tensor-core pass: 2M <= 16, 32, 48, 64 and 128
 CASES = [(1, 2, 1), (130, 2, 3), (1000, 8, 17), (2111, 5, 9), (700, 16, 33), (900, 4, 64),
-         (3000, 3, 16)]
+         (3000, 3, 16), (1500, 8, 28)]
 
 
 def _prob(n, d):
