@@ -419,18 +419,22 @@ ulisse_status ulisse_ws_x0(ulisse_ctx *ctx, const double *psi, int bf16, float *
  * data set), advanced together.  Each problem b keeps its own data, parameters psi_b
  * (p_b = d_b + 2) and solver state, and draws from its own random streams (the generator
  * key is cfg->seed + b, so problem b reproduces a single context created with that seed).
- * The O(n^2) passes of all problems run as ONE persistent launch each: every CG round's
- * covariance products over all live columns of all problems, and the fused gradient
- * sweep; the work list has one item per (problem, 256-row block), longest rows first.
+ * The O(n^2) passes of all problems run as one launch each: every CG round's covariance
+ * products over all live columns of all problems, and the fused gradient sweep.
+ *   ULISSE_PREC_FP32: persistent SIMT launches over (problem, 256-row block) items, longest
+ *     rows first;
+ *   ULISSE_PREC_MIXED: the tensor-core products (as ulisse_config.tc_cross_term = 2, the
+ *     column term added in the epilogue for every d) over (problem, 128-row block, split)
+ *     items, and the tensor-core gradient pass, one launch per padded input width (2, 4, 8).
  * Parameters and gradients are packed: problem b's p_b values follow problem b-1's.
- * Batched contexts run the FP32 path (cfg->precision must be ULISSE_PREC_FP32), take
- * n_probes <= 16 (warm_start_probes applies to every problem), and accept only the ulisse_batch_* calls (plus ulisse_set_graph,
- * counters and destroy); the single-problem calls return ULISSE_ERR_ARG on them.
+ * Batched contexts take n_probes <= 16 (warm_start_probes applies to every problem), and
+ * accept only the ulisse_batch_* calls (plus ulisse_set_graph, counters and destroy); the
+ * single-problem calls return ULISSE_ERR_ARG on them.
  *
  *   n_problems  1 .. 4096.   n, d: host arrays of n_problems sizes (1 <= d_b <= 8).
  *   X, y        host arrays of n_problems DEVICE pointers (row-major n_b x d_b, and n_b);
  *               copied into the context.
- * Errors: ULISSE_ERR_ARG (bad sizes, null pointers, precision), ULISSE_ERR_NOMEM.
+ * Errors: ULISSE_ERR_ARG (bad sizes, null pointers, precision FP64), ULISSE_ERR_NOMEM.
  */
 ulisse_status ulisse_create_batched(ulisse_ctx **out, int n_problems, const long long *n,
                                     const int *d, const float *const *X, const float *const *y,
