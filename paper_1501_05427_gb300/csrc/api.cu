@@ -805,6 +805,15 @@ static ulisse_status ensure_grad_maps(ulisse_ctx* ctx, int nr) {
   return ULISSE_OK;
 }
 
+// The tensor-core gradient pass reads the TF32 row images of the K V pass (padded d <= 8);
+// the single-context images carry b_j in their augmented column when d pads to less than 8.
+static void set_grad_images(GradLaunch& L, const ulisse_ctx* c) {
+  L.X_hi = c->Xt_hi;
+  L.X_lo = c->Xt_lo;
+  L.X_off = c->ld128 * 24;
+  L.c_has_bj = c->DP < 8 && !c->tc_no_aug;
+}
+
 // The fused gradient pass over the columns of SE (left factors, scaled) and B (right factors);
 // the maps and scales default to the gradient's own.
 static ulisse_status run_grad(ulisse_ctx* ctx, int M, const int* amap = nullptr,
@@ -831,6 +840,7 @@ static ulisse_status run_grad(ulisse_ctx* ctx, int M, const int* amap = nullptr,
   L.tc_hi = ctx->Gt_hi;
   L.tc_lo = ctx->Gt_lo;
   L.tc_ld = ctx->ld128;
+  set_grad_images(L, ctx);
   for (int attempt = 0; attempt < 2; ++attempt) {
     L.partials = ctx->gpart;
     L.partials_len = ctx->gpart_len;
@@ -2481,6 +2491,7 @@ static ulisse_status batch_prepare(ulisse_ctx* ctx) {
         L.tc_hi = sub->Gt_hi;
         L.tc_lo = sub->Gt_lo;
         L.tc_ld = sub->ld128;
+        set_grad_images(L, sub);
         gl[li] = L;
         ns[li] = ctx->b_gt_nsplit[b];
       }

@@ -20,17 +20,22 @@
 // rows of J).  For a block of 128 rows I and each visited 32-point tile J:
 //   1. W'_IJ = [A^ | B]_I [B | A^]_J^T on the tensor cores (K = 2M factors, both operands
 //      split into BF16 high + low parts: three products), into tensor memory;
-//   2. the epilogue warps read W back (tcgen05.ld), form the kernel values as the K V kernel
-//      does (cross term from row norms, one ex2), multiply, split P into BF16 high + low parts
-//      and store them over W's own tensor-memory columns;
+//   2. for padded d <= 8, C_IJ = A_I B_J^T on the tensor cores as in the K V pass (the TF32
+//      row images A_j = x^_j, B_j = 2 c1 x^_j, three TF32 products) into its own tensor-memory
+//      buffer; the epilogue warps read W and C back (tcgen05.ld), form the kernel values as the
+//      K V kernel does (exponent (a_i + b_j) + C_ij from the row norms, one ex2; for d = 16
+//      the cross term on the FP32 pipe), multiply, split P into BF16 high + low parts and
+//      store them over W's own tensor-memory columns;
 //   3. [S | G | H]_I += P_IJ Z_J on the tensor cores, Z_j = [x^_j, x^_j^2, 1] split the same
 //      way, accumulated in tensor memory across all tiles of the CTA's j range.
 // The per-row combination and the diagonal sum run in FP64 at the end; CTA partials are summed
 // in a fixed order by the last CTA to arrive (as in the SIMT gradient kernel).  Warp 0 streams
-// x^_J, the row norms, B^_J and Z_J into a 4-stage ring with bulk copies; one thread of warp 1
-// issues the MMAs; eight epilogue warps (a tensor-memory lane quadrant and half of the tile's
-// 32 columns each) make P.  W/P tiles are double-buffered; a buffer is refilled only after the
-// MMAs that read it have completed.  Every wait is bounded.
+// B_J's TF32 image (x^_J for d = 16), the row norms, B^_J and Z_J into a 3- or 4-stage ring
+// with bulk copies; one thread of warp 1 issues the MMAs; eight epilogue warps (a tensor-memory
+// lane quadrant and half of the tile's 32 columns each) make P.  W/P tiles are double-buffered;
+// a buffer is refilled only after the MMAs that read it have completed.  The single C buffer
+// takes the next tile's product as soon as the eight warps have read it, so those MMAs run
+// during the current tile's arithmetic.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -133,33 +138,81 @@ struct GtDevArgs {
   const DevParams* params;
   int nsplit, ntiles;
   int n_cta;           // CTAs of this problem (row blocks x nsplit): the last one reduces
+  // padded d <= 8: the TF32 row images of the tensor-core K V pass (8 columns, 32-row
+  // K-major canonical tiles; high part and remainder), A_j = [x^_j, 1?] and
+  // B_j = [2 c1 x^_j, b_j?]; c_has_bj when the augmented column carries b_j
+  const float* XA_hi;
+  const float* XA_lo;
+  const float* XB_hi;
+  const float* XB_lo;
+  int c_has_bj;
   double* partials;
   int* counter;
   double* g_out;
   int* status;
 };
 
+// XC (padded d <= 8): the exponent's cross term C = A_I B_J^T on the tensor cores from the
+// TF32 row images (three TF32 products, as the K V pass); the stage carries B_J's image instead
+// of x^_J.  Padded d = 16 keeps the FP32 cross term (its accumulator leaves no room for C).
 template <int DP, int KS>
 struct GtShape {
+  static constexpr bool XC = DP <= 8;
   static constexpr int K1 = 16 * KS;                   // factor slots (2M), padded
   static constexpr int N2 = (2 * DP + 1 + 15) / 16 * 16;
-  static constexpr int ST = 4;
+  static constexpr int K8 = 8;                         // columns of the TF32 row images
   static constexpr uint32_t A_BYTES = kGtBM * K1 * 2;  // one part of A^_I
-  static constexpr uint32_t X_BYTES = kGtBN * DP * 4;
+  static constexpr uint32_t XA_BYTES = XC ? kGtBM * K8 * 4 : 0;   // one part of A_I (TF32)
+  static constexpr uint32_t X_BYTES = XC ? 2 * kGtBN * K8 * 4 : kGtBN * DP * 4;
+  static constexpr uint32_t XB_BYTES = kGtBN * K8 * 4;  // one part of B_J (TF32)
   static constexpr uint32_t BN_BYTES = kGtBN * 4;
   static constexpr uint32_t BT_BYTES = kGtBN * K1 * 2;
   static constexpr uint32_t Z_BYTES = N2 * kGtBN * 2;
-  static constexpr uint32_t STAGE_BYTES = X_BYTES + BN_BYTES + 2 * BT_BYTES + 2 * Z_BYTES;
-  static constexpr uint32_t OFF_STAGES = 2 * A_BYTES;
+  // stage: x^_J (FP32) or B_J (TF32 high | remainder), b_J, B^_J high | low, Z_J high | low
+  static constexpr uint32_t OFF_BN = X_BYTES;
+  static constexpr uint32_t OFF_BT = OFF_BN + BN_BYTES;
+  static constexpr uint32_t OFF_Z = OFF_BT + 2 * BT_BYTES;
+  static constexpr uint32_t STAGE_BYTES = OFF_Z + 2 * Z_BYTES;
+  static constexpr int NBARS_FIXED = 2 + 2 + 2 + 1 + 2;  // w_full, p_full, free, done, c_full/free
+  static constexpr uint32_t FIXED = 2 * A_BYTES + 2 * XA_BYTES + (8 + NBARS_FIXED) * 8 + 64;
+  // four stages unless three keep one more CTA per SM (228 KB of shared memory per SM)
+  static constexpr int occ_with(int st) {
+    const int o = (int)((228u * 1024u) / (FIXED + st * STAGE_BYTES + 2048u));
+    const int cap = DP >= 16 ? 2 : 3;   // the launch bounds' CTAs per SM
+    return o < cap ? o : cap;
+  }
+  static constexpr int ST = occ_with(4) >= occ_with(3) ? 4 : 3;
+  static constexpr uint32_t OFF_XA = 2 * A_BYTES;
+  static constexpr uint32_t OFF_STAGES = OFF_XA + 2 * XA_BYTES;
   static constexpr uint32_t OFF_BARS = OFF_STAGES + ST * STAGE_BYTES;
-  static constexpr int NBARS = 2 * ST + 2 + 2 + 2 + 1;  // full, empty, w_full, p_full, free, done
+  static constexpr int NBARS = 2 * ST + NBARS_FIXED;    // full, empty, then the fixed ones
   static constexpr uint32_t SMEM = OFF_BARS + NBARS * 8 + 64;
-  // tensor-memory columns: two W/P buffers of 32, then the [G | H | S] accumulator
-  static constexpr uint32_t COL_D2 = 64;
+  // tensor-memory columns: two W/P buffers of 32, the C buffer of 32 (XC), then the
+  // [G | H | S] accumulator
+  static constexpr uint32_t COL_C = 64;
+  static constexpr uint32_t COL_D2 = XC ? 96 : 64;
   static_assert(COL_D2 + N2 <= kGtCols, "tensor memory layout exceeds the allocation");
-  static_assert(X_BYTES % 16 == 0 && STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0,
+  static_assert(X_BYTES % 16 == 0 && STAGE_BYTES % 16 == 0 && A_BYTES % 16 == 0 &&
+                    OFF_BT % 16 == 0 && OFF_Z % 16 == 0 && OFF_STAGES % 16 == 0,
                 "bulk copies and descriptors need 16-byte alignment");
 };
+
+// Two 16-column tensor-memory loads at independent addresses and one wait.
+__device__ inline void gt_tmem_ld16_two(uint32_t ta, uint32_t tb, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,"
+      "%27,%28,%29,%30,%31}, [%33];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+}
 
 __device__ inline bool gt_warp_wait(uint64_t* bar, uint32_t parity) {
   const bool ok = mbar_wait_spin(bar, parity);
@@ -184,6 +237,8 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
   uint64_t* p_full = w_full + 2;
   uint64_t* b_free = p_full + 2;
   uint64_t* done = b_free + 2;
+  uint64_t* c_full = done + 1;   // XC: C_J formed (MMA commit)
+  uint64_t* c_free = done + 2;   // XC: the eight epilogue warps have read C_J
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + S::OFF_BARS + S::NBARS * 8);
   volatile int* s_fail = reinterpret_cast<volatile int*>(s_tmem + 1);
   int* s_last = reinterpret_cast<int*>(s_tmem + 2);
@@ -217,6 +272,16 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
     *reinterpret_cast<__nv_bfloat16*>(sAh + off) = h;
     *reinterpret_cast<__nv_bfloat16*>(sAl + off) = l;
   }
+  if constexpr (S::XC) {
+    // A_I's TF32 image (high part, then remainder): 128 rows of the packed images, which
+    // are zero beyond n
+    constexpr int kQ = kGtBM * S::K8 / 4;   // float4 per part
+    float4* sx = reinterpret_cast<float4*>(smem + S::OFF_XA);
+    const float4* gh = reinterpret_cast<const float4*>(a.XA_hi + row0 * S::K8);
+    const float4* gl = reinterpret_cast<const float4*>(a.XA_lo + row0 * S::K8);
+    for (int idx = tid; idx < 2 * kQ; idx += kGtThreads)
+      sx[idx] = idx < kQ ? gh[idx] : gl[idx - kQ];
+  }
   tc::fence_async_smem();
   if (tid == 0) {
     for (int s = 0; s < ST; ++s) {
@@ -229,6 +294,8 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
       mbar_init(&b_free[b], 1);
     }
     mbar_init(done, 1);
+    mbar_init(c_full, 1);
+    mbar_init(c_free, 8);
     fence_barrier_init();
     *s_fail = 0;
   }
@@ -244,7 +311,7 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
   for (int k = 0; k < NACC; ++k) acc[k] = 0.0;
 
   if (warp == 0) {
-    // ------------- producer: x^_J, b_J, B^_J and Z_J tiles into the ring -------------
+    // ---------- producer: x^_J (or B_J's TF32 image), b_J, B^_J and Z_J into the ring ----------
     if (lane == 0) {
       for (int lt = 0; lt < nt; ++lt) {
         const int s = lt % ST;
@@ -256,19 +323,24 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
         const long long t = tile_begin + lt;
         unsigned char* st = stage(s);
         mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
-        bulk_g2s(st, a.xhat + t * kGtBN * DP, S::X_BYTES, &full[s]);
-        bulk_g2s(st + S::X_BYTES, a.bneg + t * kGtBN, S::BN_BYTES, &full[s]);
-        unsigned char* bt = st + S::X_BYTES + S::BN_BYTES;
+        if constexpr (S::XC) {
+          bulk_g2s(st, a.XB_hi + t * kGtBN * S::K8, S::XB_BYTES, &full[s]);
+          bulk_g2s(st + S::XB_BYTES, a.XB_lo + t * kGtBN * S::K8, S::XB_BYTES, &full[s]);
+        } else {
+          bulk_g2s(st, a.xhat + t * kGtBN * DP, S::X_BYTES, &full[s]);
+        }
+        bulk_g2s(st + S::OFF_BN, a.bneg + t * kGtBN, S::BN_BYTES, &full[s]);
+        unsigned char* bt = st + S::OFF_BT;
         bulk_g2s(bt, a.Bt_hi + t * kGtBN * K1, S::BT_BYTES, &full[s]);
         bulk_g2s(bt + S::BT_BYTES, a.Bt_lo + t * kGtBN * K1, S::BT_BYTES, &full[s]);
-        bulk_g2s(bt + 2 * S::BT_BYTES, a.Zt_hi + t * N2 * kGtBN, S::Z_BYTES, &full[s]);
-        bulk_g2s(bt + 2 * S::BT_BYTES + S::Z_BYTES, a.Zt_lo + t * N2 * kGtBN, S::Z_BYTES,
-                 &full[s]);
+        unsigned char* zt = st + S::OFF_Z;
+        bulk_g2s(zt, a.Zt_hi + t * N2 * kGtBN, S::Z_BYTES, &full[s]);
+        bulk_g2s(zt + S::Z_BYTES, a.Zt_lo + t * N2 * kGtBN, S::Z_BYTES, &full[s]);
         issued = lt + 1;
       }
     }
   } else if (warp == 1) {
-    // ------------- MMA issuer: W = A^ B^T, then [G | H | S] += P Z -------------
+    // ------------- MMA issuer: W = A^ B^T and C = A B^T, then [G | H | S] += P Z -------------
     if (lane == 0) {
       constexpr uint32_t idesc_w = tc::instr_desc(1, kGtBM, kGtBN);
       constexpr uint32_t idesc_g = tc::instr_desc(1, kGtBM, N2);
@@ -278,7 +350,7 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
         const int s = p % ST, b = p & 1;
         if (!mbar_wait_spin(&full[s], (uint32_t)((p / ST) & 1))) return false;
         tc::fence_after();
-        const uint32_t bH = smem_u32(stage(s) + S::X_BYTES + S::BN_BYTES);
+        const uint32_t bH = smem_u32(stage(s) + S::OFF_BT);
         const uint32_t bL = bH + S::BT_BYTES;
         const uint32_t dW = tbase + (uint32_t)(b * 32);
 #pragma unroll
@@ -293,14 +365,43 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
         tc::commit(&w_full[b]);
         return true;
       };
+      // C_J = A_I B_J^T into the single C buffer (three TF32 products, K = 8)
+      auto issue_c = [&](int p) -> bool {
+        const int s = p % ST;
+        if (!mbar_wait_spin(&full[s], (uint32_t)((p / ST) & 1))) return false;
+        tc::fence_after();
+        constexpr uint32_t idesc_c = tc::instr_desc(2, kGtBM, kGtBN);   // TF32
+        constexpr uint32_t sbo_x = (S::K8 / 4) * 128;
+        const uint32_t xa = smem_u32(smem + S::OFF_XA), xb = smem_u32(stage(s));
+#pragma unroll
+        for (int term = 0; term < 3; ++term) {
+          const uint32_t A = term == 2 ? xa + S::XA_BYTES : xa;
+          const uint32_t B = term == 1 ? xb + S::XB_BYTES : xb;
+          tc::mma_tf32(tbase + S::COL_C, tc::smem_desc(A, 128, sbo_x),
+                       tc::smem_desc(B, 128, sbo_x), idesc_c, term != 0);
+        }
+        tc::commit(c_full);
+        return true;
+      };
       bool ok = true;
       for (int p = 0; p < min(2, nt) && ok; ++p) ok = issue_w(p);
+      if constexpr (S::XC) {
+        if (ok && nt > 0) ok = issue_c(0);
+      }
       for (int p = 0; p < nt && ok; ++p) {
         if (*s_fail) { ok = false; break; }
         const int s = p % ST, b = p & 1;
+        if constexpr (S::XC) {
+          // the C buffer takes tile p + 1 once the epilogue has read tile p's
+          if (p + 1 < nt) {
+            if (!mbar_wait_spin(c_free, (uint32_t)(p & 1))) { ok = false; break; }
+            tc::fence_after();
+            if (!issue_c(p + 1)) { ok = false; break; }
+          }
+        }
         if (!mbar_wait_spin(&p_full[b], (uint32_t)((p / 2) & 1))) { ok = false; break; }
         tc::fence_after();
-        const uint32_t zH = smem_u32(stage(s) + S::X_BYTES + S::BN_BYTES + 2 * S::BT_BYTES);
+        const uint32_t zH = smem_u32(stage(s) + S::OFF_Z);
         const uint32_t zL = zH + S::Z_BYTES;
         const uint32_t pcol = tbase + (uint32_t)(b * 32);
 #pragma unroll
@@ -333,44 +434,71 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
     const uint32_t lane_base = (uint32_t)(eq * 32) << 16;
     const float c0 = a.params->c0f, c1 = a.params->c1f;
     const float two_c1 = 2.f * c1;
-    float xi[DP];
+    float xi[S::XC ? 1 : DP];
+    if constexpr (!S::XC) {
 #pragma unroll
-    for (int k = 0; k < DP; ++k) xi[k] = (i < a.n) ? two_c1 * a.xhat[i * DP + k] : 0.f;
+      for (int k = 0; k < DP; ++k) xi[k] = (i < a.n) ? two_c1 * a.xhat[i * DP + k] : 0.f;
+    }
     const float ai = c0 + ((i < a.n) ? a.bneg[i] : 0.f);
+    const bool add_bj = !S::XC || !a.c_has_bj;   // else the augmented C carries b_j
     bool ok = true;
     for (int lt = 0; lt < nt; ++lt) {
       const int s = lt % ST, b = lt & 1;
-      const bool ready = gt_warp_wait(&full[s], (uint32_t)((lt / ST) & 1)) &&
-                         gt_warp_wait(&w_full[b], (uint32_t)((lt / 2) & 1));
+      bool ready = gt_warp_wait(&full[s], (uint32_t)((lt / ST) & 1)) &&
+                   gt_warp_wait(&w_full[b], (uint32_t)((lt / 2) & 1));
+      if constexpr (S::XC) ready = ready && gt_warp_wait(c_full, (uint32_t)(lt & 1));
       if (!__all_sync(0xffffffffu, ready && !*s_fail)) { ok = false; break; }
       tc::fence_after();
       const uint32_t wcol = tbase + lane_base + (uint32_t)(b * 32 + half * 16);
-      float w[16];
-      tc::tmem_ld16(wcol, w);
+      float w[16], cx[16];
+      if constexpr (S::XC) {
+        uint32_t r[32];
+        gt_tmem_ld16_two(wcol, tbase + lane_base + S::COL_C + (uint32_t)(half * 16), r);
+        tc::fence_before();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(c_free);   // the C buffer may take the next tile
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          w[q] = __uint_as_float(r[q]);
+          cx[q] = __uint_as_float(r[16 + q]);
+        }
+      } else {
+        tc::tmem_ld16(wcol, w);
+      }
       if (tile_begin + lt < diag_end) {   // a tile of I itself: (i, j) and (j, i) both visited
 #pragma unroll
         for (int q = 0; q < 16; ++q) w[q] *= 0.5f;
       }
       const float* tx = reinterpret_cast<const float*>(stage(s));
-      const float* tb = reinterpret_cast<const float*>(stage(s) + S::X_BYTES);
+      const float* tb = reinterpret_cast<const float*>(stage(s) + S::OFF_BN);
       uint32_t hi[8], lo[8];
-      // packed FP32x2 instructions: the cross term two coordinates at a time, the weight and
-      // the high/low split two entries at a time
+      // packed FP32x2 instructions: the cross term two coordinates at a time (FP32 pipe) or
+      // the exponent two entries at a time (tensor-core C), the weight and the high/low split
+      // two entries at a time
       const float2 minus1 = make_float2(-1.f, -1.f);
+      const float2 ai2 = make_float2(ai, ai);
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         float ex[2];
         const float2 bj = *reinterpret_cast<const float2*>(tb + half * 16 + 2 * q);
+        if constexpr (S::XC) {
+          // (a_i + b_j) + C_ij, the order of the K V pass
+          const float2 base = add_bj ? __fadd2_rn(ai2, bj) : ai2;
+          const float2 e2 = __fadd2_rn(base, make_float2(cx[2 * q], cx[2 * q + 1]));
+          ex[0] = e2.x;
+          ex[1] = e2.y;
+        } else {
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-          const int j = half * 16 + 2 * q + h2;
-          float xj[DP];
-          load_row<float, DP>(tx + j * DP, xj);
-          float2 acc = make_float2(ai + (h2 == 0 ? bj.x : bj.y), 0.f);
+          for (int h2 = 0; h2 < 2; ++h2) {
+            const int j = half * 16 + 2 * q + h2;
+            float xj[DP];
+            load_row<float, DP>(tx + j * DP, xj);
+            float2 acc = make_float2(ai + (h2 == 0 ? bj.x : bj.y), 0.f);
 #pragma unroll
-          for (int k = 0; k < DP; k += 2)
-            acc = __ffma2_rn(make_float2(xi[k], xi[k + 1]), make_float2(xj[k], xj[k + 1]), acc);
-          ex[h2] = acc.x + acc.y;
+            for (int k = 0; k < DP; k += 2)
+              acc = __ffma2_rn(make_float2(xi[k], xi[k + 1]), make_float2(xj[k], xj[k + 1]), acc);
+            ex[h2] = acc.x + acc.y;
+          }
         }
         const float2 pk = __fmul2_rn(make_float2(ex2_approx(fminf(ex[0], c0)),
                                                  ex2_approx(fminf(ex[1], c0))),
@@ -382,7 +510,7 @@ __device__ __forceinline__ void gt_body(const GtDevArgs& a, const int rb, const 
         lo[q] = *reinterpret_cast<const uint32_t*>(&l);
       }
       __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&empty[s]);   // x^_J and b_J consumed
+      if (lane == 0) tc::mbar_arrive(&empty[s]);   // x^_J (or nothing) and b_J consumed
       // P over this warp's own 16 W columns: high parts first, then low parts
       tc::tmem_st8(wcol, hi);
       tc::tmem_st8(wcol + 8, lo);
@@ -571,6 +699,15 @@ static int plan_gt_split(long long n_rb, long long ntiles, int num_sms, int occ)
   return best_s;
 }
 
+// The TF32 row images of the K V pass (A rows at X_hi / X_lo, B rows X_off floats on).
+static void gt_set_images(GtDevArgs& a, const GradLaunch& L) {
+  a.XA_hi = L.X_hi;
+  a.XA_lo = L.X_lo;
+  a.XB_hi = L.X_hi ? L.X_hi + L.X_off : nullptr;
+  a.XB_lo = L.X_lo ? L.X_lo + L.X_off : nullptr;
+  a.c_has_bj = L.c_has_bj ? 1 : 0;
+}
+
 template <int DP, int KS>
 struct GtInst {
   using S = GtShape<DP, KS>;
@@ -642,6 +779,7 @@ struct GtInst {
     a.nsplit = nsplit;
     a.n_cta = n_rb * nsplit;
     a.ntiles = (int)ntiles;
+    gt_set_images(a, L);
     a.partials = L.partials;
     a.counter = L.counter;
     a.g_out = L.g_out;
@@ -675,6 +813,7 @@ cudaError_t gt_batch_upload_args(const GradLaunch* L, const int* nsplit, int B, 
     const long long ntiles = (l.n + kGtBN - 1) / kGtBN;
     const long long n_rb = (l.n + kGtBM - 1) / kGtBM;
     if (l.M < 1 || l.M > kMaxM || nsplit[b] < 1 || l.DP != L[0].DP || !l.tc_hi || !l.tc_lo ||
+        !l.X_hi || !l.X_lo ||
         (ntiles + nsplit[b] - 1) / nsplit[b] > kTcMaxSplitTiles)
       return cudaErrorInvalidValue;
     GtDevArgs& a = h[b];
@@ -700,6 +839,7 @@ cudaError_t gt_batch_upload_args(const GradLaunch* L, const int* nsplit, int B, 
     a.nsplit = nsplit[b];
     a.ntiles = (int)ntiles;
     a.n_cta = (int)(n_rb * nsplit[b]);
+    gt_set_images(a, l);
     a.partials = l.partials;
     a.counter = l.counter;
     a.g_out = l.g_out;
@@ -756,6 +896,7 @@ cudaError_t launch_grad_tc_batch(const void* args_dev, int B, const int4* items,
 
 cudaError_t launch_grad_tc(GradLaunch& L, cudaStream_t s) {
   if (L.M < 1 || L.M > kMaxM || !L.tc_hi || !L.tc_lo || !L.bneg) return cudaErrorInvalidValue;
+  if (L.DP <= 8 && (!L.X_hi || !L.X_lo)) return cudaErrorInvalidValue;
   switch (L.DP) {
     case 2: return grad_tc_dispatch_m<2>(L, s);
     case 4: return grad_tc_dispatch_m<4>(L, s);

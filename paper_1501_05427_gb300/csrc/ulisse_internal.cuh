@@ -265,6 +265,13 @@ struct GradLaunch {
   void* tc_hi;
   void* tc_lo;
   long long tc_ld;
+  // padded d <= 8: the TF32 row images of launch_pack_x_tf32 (A rows at X_hi / X_lo, B rows
+  // X_off floats further on), from which the pass forms the exponent's cross term on the
+  // tensor cores; c_has_bj when they were packed with the augmented column (b_j in C)
+  const float* X_hi;
+  const float* X_lo;
+  long long X_off;
+  bool c_has_bj;
 };
 
 // Mixed-precision (tcgen05) K V launch: operands prepared by launch_prescale_tc.
