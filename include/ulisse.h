@@ -57,8 +57,10 @@ typedef enum {
     ULISSE_PREC_MIXED = 1,    /* tensor-core (tcgen05) products, FP32 vectors: K V with the
                                  exponent's dot product by three TF32 products and the
                                  contraction by three BF16 products, the gradient's bilinear
-                                 forms by three BF16 products; each result's error is stated
-                                 at the call (about 1e-4 of its dot-product scale at most) */
+                                 forms by three BF16 products (its exponent's dot product by
+                                 three TF32 products for d <= 8); each result's error is
+                                 stated at the call (about 1e-4 of its dot-product scale at
+                                 most) */
     ULISSE_PREC_FP64 = 2      /* FP64 everywhere (the paper's double-precision CMVPs) */
 } ulisse_precision;
 
@@ -88,10 +90,12 @@ typedef struct {
                                 tuned default.  Changes the summation order of the split
                                 j range, hence the last bits of the results. */
     int tc_cross_term;       /* mixed precision: where the cross term x^_i . x^_j of the
-                                kernel values is formed -- 1 = FP32 FMAs on the CUDA cores,
-                                2 = three TF32 products on the tensor cores (x^ split into a
-                                TF32 high part and the remainder), 0 = the default (2) or the
-                                autotuner's choice.  The two differ in the last bits of each
+                                K V products' kernel values is formed (the gradient pass
+                                forms it on the tensor cores for d <= 8, on the CUDA cores
+                                for d > 8, whatever this says) -- 1 = FP32 FMAs on the CUDA
+                                cores, 2 = three TF32 products on the tensor cores (x^ split
+                                into a TF32 high part and the remainder), 0 = the default (2)
+                                or the autotuner's choice.  The two differ in the last bits of each
                                 kernel value (relative 1e-6 to 1e-5). */
     double pcg_delta;        /* 0: the solves run CG (Algorithm 1).  > 0: preconditioned CG
                                 with J = K + pcg_delta I (Sec. 3, "Preconditioned CG"), every
