@@ -565,6 +565,34 @@ static CgArgs<T> cg_args(ulisse_ctx* ctx, int has_s0, unsigned long long step) {
   return a;
 }
 
+// Rows per CTA of the CG start over all R columns: about two waves of CTAs, at least 2048
+// rows each (one CTA per column for small problems).  Returns the chunk count.
+static int cg_init_split(long long n, int R, int num_sms, long long* chunk) {
+  const long long target = std::max(1, (2 * num_sms + R - 1) / R);
+  long long ch = std::max<long long>((n + target - 1) / target, 2048);
+  ch = std::max<long long>(ch, (n + kMaxCgChunks - 1) / kMaxCgChunks);
+  ch = (ch + 255) / 256 * 256;
+  *chunk = ch;
+  return (int)((n + ch - 1) / ch);
+}
+
+// Kernel launches of the CG start: the partial sums first when a column spans several chunks.
+static int cg_init_launch_count(long long n, int R, int num_sms) {
+  long long ch;
+  return cg_init_split(n, R, num_sms, &ch) > 1 ? 2 : 1;
+}
+
+// The CG start of columns 0..R-1 (cg_init_kernel, after cg_init_dot_kernel when a column
+// spans several chunks).
+template <typename T>
+static cudaError_t launch_cg_init(CgArgs<T> a, int R, int num_sms, cudaStream_t s) {
+  a.nchunk = cg_init_split(a.n, R, num_sms, &a.chunk);
+  const dim3 grid((unsigned)a.nchunk, (unsigned)R);
+  if (a.nchunk > 1) cg_init_dot_kernel<T><<<grid, kCgChunkNT, 0, s>>>(a);
+  cg_init_kernel<T><<<grid, kCgChunkNT, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 // Column metadata (estimator count, estimator offset, random-stream column) for R columns.
 static ulisse_status upload_meta(ulisse_ctx* ctx, int R, const int* n_est, int* total_est) {
   std::vector<ColState> h(R);
@@ -605,9 +633,8 @@ static ulisse_status solve_core(ulisse_ctx* ctx, int R, int s0_cols, unsigned lo
     CKS(run_kmv(ctx, ctx->S, ctx->iota, s0_cols, ctx->KD, ctx->iota, kModeK, -1));
     ctx->mvp_rounds += 1;
   }
-  cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
-  CK(cudaGetLastError());
-  ctx->launches++;
+  CK(launch_cg_init(a, R, ctx->num_sms, ctx->stream));
+  ctx->launches += cg_init_launch_count(ctx->n, R, ctx->num_sms);
   int n_prev = 0;
   for (int it = 0; it <= ctx->cfg.max_iter; ++it) {
     compact_kernel<<<1, 32, 0, ctx->stream>>>(ctx->st, ctx->st_next, R, n_prev, ctx->live,
@@ -1474,8 +1501,7 @@ static ulisse_status graph_capture_body(ulisse_ctx* ctx, int s0_cols) {
     a.warm_refresh = ctx->cfg.probe_refresh;
     a.y_learned = s0_cols > 0 ? 1 : 0;
   }
-  cg_init_kernel<T><<<R, kCgNT, 0, ctx->stream>>>(a);
-  CK(cudaGetLastError());
+  CK(launch_cg_init(a, R, ctx->num_sms, ctx->stream));
   CK(cudaMemsetAsync(ctx->n_live_dev, 0, sizeof(int), ctx->stream));
   CK(cudaMemsetAsync(ctx->gstat + 3, 0, sizeof(long long), ctx->stream));
 
@@ -1616,8 +1642,10 @@ static ulisse_status graph_build(ulisse_ctx* ctx, int s0_cols) {
   // what one launch does outside the CG loop (the loop's share is counted on the device)
   const long long kmv_per = ctx->mixed ? 2 : 1, kmv_cols = ctx->mixed ? 64 : kMaxRChunk;
   const int init_cols = warm ? R : s0_cols;   // columns of the product K s_0
-  ctx->graph_launches_fixed = (ctx->mixed ? 3 : 1) + 1 + 1 + (ctx->mixed ? 3 : 1) + 1 +
-      (s0_cols > 0 ? 2 : 0) +
+  // prescale (+ the tensor-core images), probes, the CG start, the gradient pass (+ its
+  // operand images), the update, the learned start's two kernels, the product K s_0
+  ctx->graph_launches_fixed = (ctx->mixed ? 3 : 1) + 1 + cg_init_launch_count(ctx->n, R, ctx->num_sms) +
+      (ctx->mixed ? 3 : 1) + 1 + (s0_cols > 0 ? 2 : 0) +
       (init_cols > 0 ? kmv_per * ((init_cols + kmv_cols - 1) / kmv_cols) : 0);
   ctx->graph_entries_fixed = (double)ctx->n * (double)ctx->n * (double)(R + init_cols);
   ctx->graph_rounds_fixed = init_cols > 0 ? 1 : 0;
@@ -2537,7 +2565,7 @@ static ulisse_status batch_step_body(ulisse_ctx* ctx, bool sgld, bool in_graph) 
     CgArgs<float> a = cg_args<float>(sub, 0, 0);
     a.cs = ctx->chain;
     if (warm) a.warm_refresh = ctx->cfg.probe_refresh;
-    cg_init_kernel<float><<<R, kCgNT, 0, ctx->stream>>>(a);
+    CK(launch_cg_init(a, R, ctx->num_sms, ctx->stream));
     CK(cudaMemsetAsync(sub->n_live_dev, 0, sizeof(int), ctx->stream));
   }
   CK(cudaGetLastError());
@@ -2671,7 +2699,9 @@ static void batch_count_fixed(ulisse_ctx* ctx, int steps, bool sgld) {
   // sweep; the updates; the warm starts' product (mixed: every K V launch packs V first)
   const bool mixed = ctx->cfg.precision == ULISSE_PREC_MIXED;
   const long long grad_launches = mixed ? 2LL * (long long)ctx->b_gt_groups.size() : 2LL;
-  ctx->launches += (long long)steps * ((mixed ? 5LL : 3LL) * B + grad_launches +
+  long long init_launches = 0;   // the CG starts' (cg_init_launch_count) beyond one per problem
+  for (ulisse_ctx* sub : ctx->subs) init_launches += cg_init_launch_count(sub->n, R, ctx->num_sms) - 1;
+  ctx->launches += (long long)steps * ((mixed ? 5LL : 3LL) * B + init_launches + grad_launches +
                                        (sgld ? B + 1 : 0) + (warm ? (mixed ? 2 : 1) : 0));
   ctx->entry_rhs += steps * ent * (warm ? 2.0 : 1.0);
   if (warm) ctx->mvp_rounds += steps;

@@ -9,7 +9,7 @@
 
 namespace ulisse {
 
-constexpr int kCgNT = 512;
+constexpr int kCgChunkNT = 256;   // threads of the chunked CG kernels
 
 // ------------------------------------------------------------------------------------
 // a2: probes r_j (column j = 1..nr of B): +-1 from the top bit, or N(0,1) by Box-Muller,
@@ -98,11 +98,67 @@ __device__ inline double weight_product(int j, double beta) {
   return W;
 }
 
-// e_0 = b - K s_0, d_0 = e_0, draws of J; one CTA per column.
 template <typename T>
-__global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
-  __shared__ double red[kCgNT / 32];
-  const int c = blockIdx.x;
+__device__ inline void chunk_range(const CgArgs<T>& a, int ch, long long* i0, long long* i1) {
+  *i0 = (long long)ch * a.chunk;
+  *i1 = min(a.n, *i0 + a.chunk);
+}
+
+// Whether column c starts from its initial iterate (else from s_0 = 0): every column with
+// has_s0; with warm-started solves, column 0 (y) when its start is valid or learned, and the
+// probe columns while the probes are unchanged.
+template <typename T>
+__device__ inline bool init_use_s0(const CgArgs<T>& a, int c) {
+  if (a.warm_refresh <= 0) return a.has_s0 != 0;
+  const unsigned long long step = a.cs ? a.cs->step0 + (unsigned long long)a.cs->k : a.step;
+  const bool valid = *a.warm_valid != 0;
+  return (c == 0) ? (a.y_learned || valid)
+                  : (valid && step % (unsigned long long)a.warm_refresh != 0);
+}
+
+// b^T b and, when use_s0, (b - K s_0)^T (b - K s_0) over rows [i0, i1) of column c (FP64),
+// summed over the block; rr = bb otherwise.
+template <typename T>
+__device__ inline void init_sums(const CgArgs<T>& a, int c, bool use_s0, long long i0,
+                                 long long i1, double* red, double* bb, double* rr) {
+  const T* b = a.B + c * a.ld;
+  const T* ks0 = a.KD + c * a.ld;
+  double pb = 0.0, pr = 0.0;
+  for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) {
+    const double bi = (double)b[i];
+    pb += bi * bi;
+    if (use_s0) {
+      const double ri = (double)(T)(b[i] - ks0[i]);
+      pr += ri * ri;
+    }
+  }
+  *bb = block_sum<kCgChunkNT>(pb, red);
+  *rr = use_s0 ? block_sum<kCgChunkNT>(pr, red) : *bb;
+}
+
+// The CG start's sums per (chunk, column) when a column spans several chunks (part2: b^T b,
+// part1: the residual's); cg_init_kernel adds them in chunk order.
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_init_dot_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgChunkNT / 32];
+  const int c = blockIdx.y, ch = blockIdx.x;
+  long long i0, i1;
+  chunk_range(a, ch, &i0, &i1);
+  double bb, rr;
+  init_sums(a, c, init_use_s0(a, c), i0, i1, red, &bb, &rr);
+  if (threadIdx.x == 0) {
+    a.part2[(long long)c * a.nchunk + ch] = bb;
+    a.part1[(long long)c * a.nchunk + ch] = rr;
+  }
+}
+
+// e_0 = b - K s_0, d_0 = e_0, draws of J; grid (chunk, column).  With one chunk per column
+// the CTA forms the sums itself; with several, every CTA of the column adds the partial sums
+// of cg_init_dot_kernel in chunk order, so all of them take the same decision.
+template <typename T>
+__global__ void __launch_bounds__(kCgChunkNT) cg_init_kernel(const CgArgs<T> a) {
+  __shared__ double red[kCgChunkNT / 32];
+  const int c = blockIdx.y, ch = blockIdx.x;
   ColState& st = a.st[c];
   T* s = a.S + c * a.ld;
   T* e = a.E + c * a.ld;
@@ -113,29 +169,26 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   T* sb = warm ? a.Sbest + c * a.ld : nullptr;
   // with warm-started solves the start comes from Sbest (y_learned: column 0 from S)
   const T* s0 = (warm && !(c == 0 && a.y_learned)) ? sb : s;
-  bool use_s0 = a.has_s0 != 0;
-  if (warm) {
-    const unsigned long long step = a.cs ? a.cs->step0 + (unsigned long long)a.cs->k : a.step;
-    const bool valid = *a.warm_valid != 0;
-    use_s0 = (c == 0) ? (a.y_learned || valid)
-                      : (valid && step % (unsigned long long)a.warm_refresh != 0);
-  }
+  const bool use_s0 = init_use_s0(a, c);
+  long long i0, i1;
+  chunk_range(a, ch, &i0, &i1);
   // An initial iterate is kept only when it lowers the residual norm below that of s_0 = 0.
   // The choice depends on the parameters, the data and the iterate alone (no random draw),
   // so every estimator built on it stays unbiased.
-  double pb = 0.0, pr = 0.0;
-  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
-    const double bi = (double)b[i];
-    pb += bi * bi;
-    if (use_s0) {
-      const double ri = (double)(T)(b[i] - ks0[i]);
-      pr += ri * ri;
+  double bb, rr;
+  if (a.nchunk == 1) {
+    init_sums(a, c, use_s0, i0, i1, red, &bb, &rr);
+  } else {
+    bb = 0.0;
+    rr = 0.0;
+    for (int k = 0; k < a.nchunk; ++k) {
+      bb += a.part2[(long long)c * a.nchunk + k];
+      rr += a.part1[(long long)c * a.nchunk + k];
     }
+    if (!use_s0) rr = bb;
   }
-  const double bb = block_sum<kCgNT>(pb, red);
-  const double rr = use_s0 ? block_sum<kCgNT>(pr, red) : bb;
   const bool keep = use_s0 && rr < bb;
-  for (long long i = threadIdx.x; i < a.n; i += kCgNT) {
+  for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) {
     const T si = keep ? s0[i] : T(0);
     s[i] = si;
     if (warm) sb[i] = si;
@@ -149,11 +202,10 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
   if (done) {
     for (int t = 0; t < n_est; ++t) {
       T* se = a.SE + (long long)(st.est_off + t) * a.ld;
-      for (long long i = threadIdx.x; i < a.n; i += kCgNT) se[i] = s[i];
+      for (long long i = i0 + threadIdx.x; i < i1; i += kCgChunkNT) se[i] = s[i];
     }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  if (ch == 0 && threadIdx.x == 0) {
     st.ee = ee;
     st.best_ee = ee;
     st.l = 0;
@@ -178,13 +230,6 @@ __global__ void __launch_bounds__(kCgNT) cg_init_kernel(const CgArgs<T> a) {
 //                     new column state (into st_next; compact_kernel commits it).
 // The increment delta_{m+1} = alpha_m d_m is added with weight prod_{r<=j} w_r to every
 // estimator whose J >= j (j = m+1-l) once the early stop at l has been reached.
-constexpr int kCgChunkNT = 256;
-
-template <typename T>
-__device__ inline void chunk_range(const CgArgs<T>& a, int ch, long long* i0, long long* i1) {
-  *i0 = (long long)ch * a.chunk;
-  *i1 = min(a.n, *i0 + a.chunk);
-}
 
 // The bodies below take the chunk (ch) and the live-list index (li) of the CTA: the
 // single-problem kernels pass their grid coordinates, the batched ones add the problem.
@@ -438,72 +483,83 @@ __global__ void __launch_bounds__(256) compact_batch_kernel(
 
 // ------------------------------------------------------------------------------------
 // a7: SGLD proposal psi' = psi + eps/2 M (g + grad log p) + sqrt(eps) L xi, L L^T = M,
-// xi_k standard normal from Philox counter (k, 0, step, 3).  One thread.
+// xi_k standard normal from Philox counter (k, 0, step, 3).  One warp: lane i owns row i of
+// L and component i (p <= kMaxP <= 32); each element's sums run in the serial order.
 // ------------------------------------------------------------------------------------
 __device__ inline void sgld_body(double* __restrict__ psi, const double* __restrict__ g,
                                  const double* __restrict__ M, const double* __restrict__ prior,
                                  double eps, int p, unsigned long long seed,
                                  unsigned long long step, double* __restrict__ trace,
                                  int* __restrict__ status) {
-  double Mm[kMaxP * kMaxP], L[kMaxP * kMaxP], xi[kMaxP], v[kMaxP];
-  for (int i = 0; i < p; ++i)
-    for (int j = 0; j < p; ++j) Mm[i * p + j] = M ? M[i * p + j] : (i == j ? 1.0 : 0.0);
-  for (int i = 0; i < p * p; ++i) L[i] = 0.0;
+  __shared__ double L[kMaxP * kMaxP];
+  __shared__ double xi[kMaxP], v[kMaxP];
+  const int lane = threadIdx.x & 31;
+  auto Mij = [&](int i, int j) -> double {
+    return M ? M[i * p + j] : (i == j ? 1.0 : 0.0);
+  };
+  if (lane < p) {
+    uint64_t w[4];
+    philox4x64_10((uint64_t)lane, 0, step, kPurposeSgld, seed, 0, w);
+    xi[lane] = box_muller(w[0], w[1]);
+    v[lane] = g[lane] + (prior ? prior[lane] : 0.0);
+    for (int j = 0; j < p; ++j) L[lane * p + j] = 0.0;
+  }
+  __syncwarp();
+  // Cholesky M = L L^T, column by column: the diagonal on lane 0, then the column below it
   for (int j = 0; j < p; ++j) {
-    double s = Mm[j * p + j];
-    for (int k = 0; k < j; ++k) s -= L[j * p + k] * L[j * p + k];
-    if (!(s > 0.0)) {
-      atomicOr(status, kStatusBadM);
+    int bad = 0;
+    if (lane == 0) {
+      double sj = Mij(j, j);
+      for (int k = 0; k < j; ++k) sj -= L[j * p + k] * L[j * p + k];
+      bad = !(sj > 0.0);
+      if (!bad) L[j * p + j] = sqrt(sj);
+    }
+    if (__shfl_sync(0xffffffffu, bad, 0)) {
+      if (lane == 0) atomicOr(status, kStatusBadM);
       return;
     }
-    L[j * p + j] = sqrt(s);
-    for (int i = j + 1; i < p; ++i) {
-      double t = Mm[i * p + j];
-      for (int k = 0; k < j; ++k) t -= L[i * p + k] * L[j * p + k];
-      L[i * p + j] = t / L[j * p + j];
+    __syncwarp();
+    if (lane > j && lane < p) {
+      double t = Mij(lane, j);
+      for (int k = 0; k < j; ++k) t -= L[lane * p + k] * L[j * p + k];
+      L[lane * p + j] = t / L[j * p + j];
     }
+    __syncwarp();
   }
-  for (int k = 0; k < p; ++k) {
-    uint64_t w[4];
-    philox4x64_10((uint64_t)k, 0, step, kPurposeSgld, seed, 0, w);
-    xi[k] = box_muller(w[0], w[1]);
-  }
-  for (int i = 0; i < p; ++i) v[i] = g[i] + (prior ? prior[i] : 0.0);
-  double out[kMaxP];
-  for (int i = 0; i < p; ++i) {
+  if (lane < p) {
     double drift = 0.0, noise = 0.0;
-    for (int j = 0; j < p; ++j) drift += Mm[i * p + j] * v[j];
-    for (int j = 0; j <= i; ++j) noise += L[i * p + j] * xi[j];
-    out[i] = psi[i] + 0.5 * eps * drift + sqrt(eps) * noise;
-  }
-  for (int i = 0; i < p; ++i) {
-    psi[i] = out[i];
-    if (trace) trace[i] = out[i];
+    for (int j = 0; j < p; ++j) drift += Mij(lane, j) * v[j];
+    for (int j = 0; j <= lane; ++j) noise += L[lane * p + j] * xi[j];
+    const double out = psi[lane] + 0.5 * eps * drift + sqrt(eps) * noise;
+    psi[lane] = out;
+    if (trace) trace[lane] = out;
   }
 }
 
+// Launched with one warp.
 __global__ void sgld_kernel(double* __restrict__ psi, const double* __restrict__ g,
                             const double* __restrict__ M, const double* __restrict__ prior,
                             const double* __restrict__ eps_arr, double eps_scalar, int p,
                             unsigned long long seed, unsigned long long step,
                             double* __restrict__ trace, int* __restrict__ status) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   sgld_body(psi, g, M, prior, eps_arr ? *eps_arr : eps_scalar, p, seed, step, trace, status);
 }
 
 // The same update inside a chain graph: step, step size and trace slot from the chain
-// slot, which then moves on to the next step.
+// slot, which then moves on to the next step.  Launched with one warp.
 __global__ void sgld_chain_kernel(double* __restrict__ psi, const double* __restrict__ g,
                                   const double* __restrict__ M, const double* __restrict__ prior,
                                   int p, unsigned long long seed, ChainSlot* __restrict__ cs,
                                   int* __restrict__ status, int advance = 1,
                                   int trace_stride = 0, int trace_off = 0) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (blockIdx.x != 0 || threadIdx.x >= 32) return;
   const long long k = cs->k;
   const long long stride = trace_stride > 0 ? trace_stride : p;
   sgld_body(psi, g, M, prior, cs->eps[k], p, seed, cs->step0 + (unsigned long long)k,
             cs->trace ? cs->trace + k * stride + trace_off : nullptr, status);
-  if (advance) cs->k = k + 1;
+  __syncwarp();   // every lane has read the slot
+  if (advance && threadIdx.x == 0) cs->k = k + 1;
 }
 
 // The chain slot moves on to the next step (batched step graphs: after every problem's
